@@ -1,0 +1,350 @@
+"""Benchmark of the FDTD + CPML hot path on GB300.
+
+Workload (one bench "step"): the 512^3 layered-model run — 10 layers
+1500-4500 m/s (seed 2), dx = 10 m, CFL 0.5, 20 CPML cells per face,
+R = 1e-8, 10 Hz Ricker 30 cells below the top face — advanced 1000 time steps
+from a zero state.  Metric: million output points per second,
+N^3 * Nt / (1e6 T) (paper Sec. 5), and the fraction of the measured HBM
+bandwidth reached by the step kernel.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--storage f32|f16|bf16]
+                    [--impl ours|reference] [--nt 1000] [--no-cpu-baseline]
+
+Multi-GPU: replicas only (the grid is not decomposed; each rank runs its own
+copy of the workload), launched by torch.distributed.run; rank 0 prints the
+JSON line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "million output points/s and % of HBM peak, plain FP32 vs chosen forms"
+UNIT = "Mpoints/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--preset", default="layered512")
+    ap.add_argument("--nt", type=int, default=None, help="time steps per bench step (default: the workload's)")
+    ap.add_argument("--cells", type=int, default=None, help="override CPML cells per face (0: no CPML)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def step_kernel_traffic(storage: str, shape):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    scaled to this grid, or None when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2606_06910_gb300", "csrc", "fdtd_step.cu")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    e = d.get(storage)
+    if not e or e.get("kernel_sha") != h:
+        return None
+    n_prof = float(np.prod(e["shape"]))
+    return float(e["dram_bytes_per_launch"]) * float(np.prod(shape)) / n_prof
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def algorithmic_bytes(shape, cells, es):
+    """Per launch: read p, v (3), K and write p, v (3): 8 stored words + one
+    FP32 word per node; plus 4 stored words (psi_v and psi_p read and write)
+    per slab node and axis."""
+    nz, ny, nx = shape
+    n = nx * ny * nz
+    slab = (cells[0] + cells[1]) * ny * nz + (cells[2] + cells[3]) * nx * nz + (cells[4] + cells[5]) * nx * ny
+    return (8 * es + 4) * n + 4 * es * slab
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2606_06910_gb300 import synth
+    from paper_2606_06910_gb300.fdtd import Fdtd
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = synth.preset(args.preset)
+    nt = args.nt or w.nt
+    cells = w.cpml_cells if args.cells is None else (args.cells,) * 6
+    shape = w.shape
+    vel_h = w.velocity()
+    src = w.sources()
+    wav_h = synth.ricker(nt, w.dt, w.f0).astype(np.float32)[None, :]
+    stream = torch.cuda.current_stream(dev)
+
+    sim = Fdtd(shape, w.h, w.dt, cpml_cells=cells, storage=args.storage, nt_max=nt, device=dev, stream=stream)
+    vel = torch.from_numpy(vel_h).to(dev)
+    wav = torch.from_numpy(wav_h).to(dev)
+    sim.set_model(vel)
+    if any(cells):
+        sim.set_cpml(R=w.R, kappa_max=w.kappa_max, alpha_frac=w.alpha_frac, q=w.q, c_ref=w.c_max)
+    sim.inject(src, wav)
+
+    def one_step(evs=None):
+        sim.reset()
+        if evs is not None:
+            evs[0].record(stream)
+        sim.step(nt)
+        if evs is not None:
+            evs[1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    sim.sync()
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0.record(stream)
+    for k in range(args.steps):
+        one_step(kev[k])
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    sim.sync()
+    total_ms = t0.elapsed_time(t1)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in kev)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    npts = float(np.prod(shape))
+    value = world * npts * nt * args.steps / (total_ms * 1e-3) / 1e6
+
+    # roofline of the step kernel (the only kernel of sim.step)
+    es = 4 if args.storage == "f32" else 2
+    launches = args.steps * nt
+    avg_launch_s = kernel_ms * 1e-3 / launches
+    bytes_launch = algorithmic_bytes(shape, cells, es)
+    achieved = bytes_launch / avg_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = step_kernel_traffic(args.storage, shape)
+
+    # end to end through the public API: pinned host model + wavelet in,
+    # final pressure snapshot out, every step
+    e2e = None
+    if not args.no_e2e:
+        vel_pin = torch.from_numpy(vel_h).pin_memory()
+        wav_pin = torch.from_numpy(wav_h).pin_memory()
+        snap_pin = torch.empty(shape, dtype=torch.float32).pin_memory()
+        vel_d = torch.empty_like(vel)
+        wav_d = torch.empty_like(wav)
+        snap_d = torch.empty(shape, dtype=torch.float32, device=dev)
+        ksteps = max(1, min(args.steps, 2))
+        torch.cuda.synchronize(dev)
+        e0 = time.perf_counter()
+        for _ in range(ksteps):
+            vel_d.copy_(vel_pin, non_blocking=True)
+            wav_d.copy_(wav_pin, non_blocking=True)
+            sim.set_model(vel_d)
+            sim.inject(src, wav_d)
+            sim.reset()
+            sim.step(nt)
+            sim.get("p", 0, snap_d)
+            snap_pin.copy_(snap_d, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        e_s = time.perf_counter() - e0
+        e2e = {"value": round(world * npts * nt * ksteps / e_s / 1e6, 2), "unit": UNIT,
+               "h2d_bytes_per_step": int(vel_pin.numel() * 4 + wav_pin.numel() * 4 + src.size * 4),
+               "d2h_bytes_per_step": int(snap_pin.numel() * 4)}
+    sim.sync()
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": f"{args.preset}: {shape[0]}^3 layered 1500-4500 m/s, CPML {cells[0]} cells, "
+                               f"R=1e-8, 10 Hz Ricker, {nt} time steps per bench step",
+                   "grid": list(shape), "time_steps_per_step": nt, "cpml_cells": list(cells),
+                   "storage": args.storage, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (state >= 4 GB per replica)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None if traffic is None else round(traffic),
+                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": "fdtd_step_kernel",
+                     "algorithmic_bytes_per_launch": int(bytes_launch),
+                     "avg_launch_us": round(avg_launch_s * 1e6, 2)},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    return out
+
+
+# ----------------------------------------------------------------------------
+# the FP64 oracle (CPU baseline and reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(preset: str, nsteps: int, warm: int = 0):
+    """Time the oracle on the full grid of the workload for nsteps time steps
+    (after `warm` untimed ones).  Returns (Mpoints/s, seconds, threads)."""
+    from oracle import oracle as O
+    from paper_2606_06910_gb300 import synth
+    w = synth.preset(preset)
+    vel = w.velocity().astype(np.float64)
+    g = O.Grid(vel * vel, w.h, w.dt, O.make_profiles(w.shape, w.cpml_cells, w.h, w.dt, w.c_max, R=w.R))
+    st = O.State(w.shape)
+    src = tuple(w.sources()[0])
+    wav = synth.ricker(max(nsteps + warm, 1), w.dt, w.f0)
+    if warm:
+        O.run(g, st, warm, 0, src, wav)
+    t = time.perf_counter()
+    O.run(g, st, nsteps, warm, src, wav)
+    dt = time.perf_counter() - t
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return float(np.prod(w.shape)) * nsteps / dt / 1e6, dt, threads
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    per, times = [], []
+    for k in range(args.warmup + args.steps):
+        mpts, secs, threads = oracle_sample(args.preset, 1)
+        if k >= args.warmup:
+            per.append(mpts)
+            times.append(secs)
+    value = float(np.prod(__import__("paper_2606_06910_gb300.synth", fromlist=["x"]).preset(args.preset).shape)) \
+        * len(times) / sum(times) / 1e6
+    sample = f"{args.preset} full grid, 1 oracle time step per bench step (FP64, OpenMP)"
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.preset} (one time step per bench step)"},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    out = run_ours(args, rank, world, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            mpts, secs, threads = oracle_sample(args.preset, 1)
+            out["cpu_baseline"] = {"value": round(mpts, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
+                                   "sample": f"{args.preset} full grid, 1 FP64 oracle time step "
+                                             f"({secs:.1f} s)"}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

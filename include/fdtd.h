@@ -1,0 +1,232 @@
+/*
+ * fdtd.h -- C ABI of the GB300 FDTD + CPML library (libfdtd.so).
+ *
+ * The library advances the first-order acoustic pressure-velocity system
+ *     p_t = -K div v,   v_t = -(1/rho) grad p          (paper Sec. 3.1)
+ * with centred radius-4 (eighth-order) derivatives and a leapfrog step
+ * (velocity half step from p^n, then pressure step from v^{n+1/2}), and the
+ * convolutional PML of Sec. 3.2 in the six boundary slabs: inside the slab of
+ * axis d every derivative delta_d f becomes (1/kappa_d) delta_d f + psi_d with
+ * psi_d <- b_d psi_d + a_d delta_d f.  Source injection and receiver sampling
+ * run inside the same kernel.  A discrete adjoint (the exact transpose of the
+ * step) gives misfit gradients with respect to the velocity model and to the
+ * CPML coefficient profiles.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - Arrays are C order [nz][ny][nx] (x fastest) unless stated; "dev" means a
+ *    CUDA device pointer, "host" a host pointer.
+ *  - Spatial indices are 0-based (z, y, x) triples.
+ *  - Faces are ordered -x, +x, -y, +y, -z, +z; CPML cells lie inside the grid.
+ *  - Every call returns an fdtd_status; nothing throws or aborts across the
+ *    ABI.  After a failure fdtd_last_error() holds a one-line reason.
+ *  - Work is enqueued on the stream given in fdtd_desc and calls may return
+ *    before it completes; calls that return host values (fdtd_set_model,
+ *    fdtd_sync, fdtd_energy, fdtd_misfit) synchronise that stream.  Errors
+ *    raised on the device (a bounded wait that gave up, non-finite values)
+ *    are reported by the next synchronising call.
+ *  - Ownership: the caller allocates all device memory.  fdtd_workspace_bytes
+ *    sizes one workspace that the caller passes to fdtd_create and keeps alive
+ *    until fdtd_destroy; the library carves every field, memory variable,
+ *    table and checkpoint out of it and never allocates device memory.  The
+ *    traces buffer given to fdtd_record is written in place and must outlive
+ *    the steps that record into it.  Host arrays are copied before the call
+ *    returns.
+ *  - One context per host thread at a time.
+ */
+#ifndef FDTD_H
+#define FDTD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDTD_ABI_VERSION 1
+
+typedef struct fdtd_ctx fdtd_ctx;
+
+typedef enum {
+    FDTD_OK = 0,
+    FDTD_EINVAL = 1,       /* an argument is out of range or inconsistent */
+    FDTD_ENOMEM = 2,       /* workspace too small, or host allocation failed */
+    FDTD_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    FDTD_ESTATE = 4,       /* call out of order (e.g. step before set_model) */
+    FDTD_EUNSTABLE = 5,    /* c_max dt / h above the scheme's stability limit */
+    FDTD_EDIVERGED = 6,    /* non-finite values detected */
+    FDTD_ETIMEOUT = 7,     /* a bounded device-side wait gave up */
+    FDTD_EUNSUPPORTED = 8  /* valid request this build does not provide */
+} fdtd_status;
+
+typedef enum {
+    FDTD_F32 = 0,          /* p, v, psi stored in FP32 */
+    FDTD_F16 = 1,          /* stored in FP16, arithmetic in FP32 registers */
+    FDTD_BF16 = 2          /* stored in BF16, arithmetic in FP32 registers */
+} fdtd_storage;
+
+/* Field selectors for fdtd_get_field / fdtd_set_field.  Velocities and memory
+ * variables are always exchanged in physical units, whatever the storage. */
+typedef enum {
+    FDTD_P = 0, FDTD_VX = 1, FDTD_VY = 2, FDTD_VZ = 3,
+    FDTD_PSIV_X = 4, FDTD_PSIV_Y = 5, FDTD_PSIV_Z = 6,   /* memory of delta_d p   */
+    FDTD_PSIP_X = 7, FDTD_PSIP_Y = 8, FDTD_PSIP_Z = 9,   /* memory of delta_d v_d */
+    FDTD_ADJ_P = 10, FDTD_ADJ_VX = 11, FDTD_ADJ_VY = 12, FDTD_ADJ_VZ = 13,
+    FDTD_ADJ_PSIV_X = 14, FDTD_ADJ_PSIV_Y = 15, FDTD_ADJ_PSIV_Z = 16,
+    FDTD_ADJ_PSIP_X = 17, FDTD_ADJ_PSIP_Y = 18, FDTD_ADJ_PSIP_Z = 19
+} fdtd_field;
+
+typedef struct {
+    int nx, ny, nz;          /* grid nodes; CPML cells included */
+    int nshots;              /* independent wavefields sharing one model (>= 1) */
+    double h;                /* grid spacing [m], equal on all axes */
+    double dt;               /* time step [s] */
+    int cpml_cells[6];       /* CPML cells per face (-x,+x,-y,+y,-z,+z), 0 = none */
+    int storage;             /* fdtd_storage */
+    int tblock_k;            /* time steps per pass over HBM: 1 (default) */
+    int nt_max;              /* capacity of wavelet and trace buffers (steps) */
+    int nrec_max;            /* receiver capacity */
+    int checkpoint_every;    /* > 0: keep checkpoints every C steps (adjoint) */
+    int cpml_grad;           /* != 0: also keep what dJ/d(CPML profile) needs */
+    void *stream;            /* cudaStream_t to enqueue on; NULL = default */
+} fdtd_desc;
+
+/* ABI version of the loaded library (FDTD_ABI_VERSION). */
+int fdtd_abi_version(void);
+
+/* Short name of a status code; never NULL. */
+const char *fdtd_status_string(int status);
+
+/* Bytes of device workspace that fdtd_create needs for `desc` (host-only
+ * computation; no CUDA call).  EINVAL if desc is invalid: a dimension < 1,
+ * h or dt <= 0, 2 * cells > n on an axis, storage unknown, tblock_k not 1,
+ * nt_max < 1, nshots outside [1, 1024], nrec_max < 0, checkpoint_every < 0,
+ * or cpml_grad set without checkpoint_every. */
+int fdtd_workspace_bytes(const fdtd_desc *desc, size_t *bytes);
+
+/* Create a context on the current CUDA device.  `workspace` (dev, 256-byte
+ * aligned, >= fdtd_workspace_bytes) stays owned by the caller and must
+ * outlive the context.  All fields start at zero, time index 0.  With the
+ * environment variable FDTD_FAULT=alloc the call fails with ENOMEM before
+ * touching the GPU (host-side failure injection for tests). */
+int fdtd_create(const fdtd_desc *desc, void *workspace, size_t workspace_bytes,
+                fdtd_ctx **out);
+
+/* Release the context (host memory only; the workspace stays the caller's). */
+int fdtd_destroy(fdtd_ctx *ctx);
+
+/* One-line description of the last failure on this context ("" if none). */
+const char *fdtd_last_error(const fdtd_ctx *ctx);
+
+/* Velocity model (paper Sec. 3.1: K = rho c^2).  vel_dev: float [nz][ny][nx]
+ * in m/s, read during the call.  rho_dev must be NULL (constant density 1;
+ * variable density is not provided: EUNSUPPORTED).  Synchronises; EINVAL if a
+ * velocity is not finite and positive; EUNSTABLE if max(c) dt / h exceeds the
+ * collocated radius-4 leapfrog limit 2 / (sqrt(3) max_theta 2 sum_l a_l sin(l theta)) = 0.6672. */
+int fdtd_set_model(fdtd_ctx *ctx, const float *vel_dev, const float *rho_dev);
+
+/* CPML grading of Sec. 3.2 / Tab. 2 on the cells given at create time:
+ *   sigma = sigma_max rho^q, sigma_max = -(q+1) c_ref ln(R) / (2 L h),
+ *   kappa = 1 + (kappa_max - 1) rho^q, alpha = alpha_frac sigma_max (1 - rho),
+ *   b = exp(-(sigma/kappa + alpha) dt), a = sigma (b - 1) / (kappa (sigma + kappa alpha)),
+ * with normalised depth rho = (L - j)/L at cell j (j = 0 outermost).
+ * c_ref <= 0 selects the model's maximum velocity (requires fdtd_set_model).
+ * Coefficients are computed on the host in double and stored as float.
+ * EINVAL for R outside (0, 1], kappa_max < 1, alpha_frac < 0 or q < 0. */
+int fdtd_set_cpml(fdtd_ctx *ctx, double R, double kappa_max, double alpha_frac,
+                  int q, double c_ref);
+
+/* Per-cell (sigma, kappa, alpha) for a layer of L equal cells on every face
+ * (all six cpml_cells equal to L): ska_dev float [L][3], cell j = 0
+ * outermost.  Converted to (b, a, 1/kappa) on the device.  Used by the
+ * learned CPML.  EINVAL if the faces differ. */
+int fdtd_set_cpml_ska(fdtd_ctx *ctx, const float *ska_dev);
+
+/* Source per shot: src_zyx (host int [nshots][3]) and wavelet_dev (dev float
+ * [nshots][nt], copied).  After the pressure update of step n, w[shot][n] is
+ * added to p at the source node (additive pressure source; samples n >= nt
+ * add nothing).  EINVAL if a node is outside the grid or nt > nt_max. */
+int fdtd_inject(fdtd_ctx *ctx, const int *src_zyx, const float *wavelet_dev, int nt);
+
+/* Receivers, shared by all shots: rec_zyx (host int [nrec][3]).  After the
+ * source of step n, traces_dev[shot][n][r] = p at receiver r for every
+ * n < nt_max (traces_dev: dev float [nshots][nt_max][nrec], written in
+ * place).  nrec = 0 disables recording.  EINVAL if a node is outside the
+ * grid or nrec > nrec_max. */
+int fdtd_record(fdtd_ctx *ctx, const int *rec_zyx, int nrec, float *traces_dev);
+
+/* Advance every shot by n full time steps (one fused kernel per step).
+ * With checkpoint_every = C > 0 the state is saved before every step whose
+ * index is a multiple of C (up to nt_max).  ESTATE before set_model /
+ * set_cpml; EINVAL if n < 0. */
+int fdtd_step_n(fdtd_ctx *ctx, int n);
+
+/* Discrete adjoint of the last n = current-time steps (run backwards from the
+ * current time index to 0 from the checkpoints, recomputing each segment):
+ * the exact transpose of the forward step.  resid_dev (dev float
+ * [nshots][nt_max][nrec], the misfit derivative dJ/dtrace) is injected at the
+ * receivers.  grad_vel_dev (dev float [nz][ny][nx]) receives += dJ/dc summed
+ * over shots (K = rho c^2; CPML coefficients held fixed).  grad_cpml_dev
+ * (dev float [3][3][nmax], nullable; nmax = max(nx, ny, nz); [axis x,y,z]
+ * [b, a, 1/kappa][node]) receives += dJ/d(profile) and needs cpml_grad at
+ * create time (EINVAL otherwise).  Needs FP32 storage,
+ * checkpoint_every > 0 and n equal to the current time index (ESTATE
+ * otherwise).  Leaves the forward state undefined (call fdtd_reset). */
+int fdtd_adjoint_step_n(fdtd_ctx *ctx, int n, const float *resid_dev,
+                        float *grad_vel_dev, float *grad_cpml_dev);
+
+/* Copy one field of one shot to/from a dense float [nz][ny][nx] device array
+ * in physical units.  Memory variables are full-volume arrays that are zero
+ * outside their slab (values outside the slab are ignored on set). */
+int fdtd_get_field(fdtd_ctx *ctx, int which, int shot, float *dst_dev);
+int fdtd_set_field(fdtd_ctx *ctx, int which, int shot, const float *src_dev);
+
+/* Zero every field and memory variable, time index 0 (model, CPML, source and
+ * receivers are kept). */
+int fdtd_reset(fdtd_ctx *ctx);
+
+/* Current time index (steps taken since create/reset). */
+int fdtd_time(const fdtd_ctx *ctx, int *t);
+
+/* Wait for the stream and report device-side errors (ETIMEOUT, EDIVERGED). */
+int fdtd_sync(fdtd_ctx *ctx);
+
+/* sum of p^2 over the box [z0,z1) x [y0,y1) x [x0,x1) of one shot, accumulated
+ * in FP64 on the device; box = {z0, z1, y0, y1, x0, x1}.  Synchronises. */
+int fdtd_energy(fdtd_ctx *ctx, int shot, const int box[6], double *out);
+
+/* Data misfit J = 1/2 sum (traces - dobs)^2 over [nshots][nt][nrec] of the
+ * recorded traces (first nt steps), accumulated in FP64 on the device;
+ * resid_dev (nullable, dev float [nshots][nt_max][nrec]) receives
+ * traces - dobs for n < nt and 0 beyond.  dobs_dev: dev float
+ * [nshots][nt_max][nrec].  Synchronises. */
+int fdtd_misfit(fdtd_ctx *ctx, const float *dobs_dev, int nt, float *resid_dev, double *out);
+
+/* Chain rule of the learned CPML: from grad_cpml (layout of
+ * fdtd_adjoint_step_n) and the per-cell ska_dev [L][3] given to
+ * fdtd_set_cpml_ska, write gska_dev [L][3] = dJ/d(sigma, kappa, alpha). */
+int fdtd_cpml_ska_backward(fdtd_ctx *ctx, const float *ska_dev, const float *grad_cpml_dev,
+                           float *gska_dev);
+
+/* ---- learned-CPML network (4 -> 64 -> 64 -> 3, tanh; no paper counterpart
+ * beyond Sec. 7's future-work note; the CPML it feeds is Sec. 3.2) ----
+ * theta: dev float [4675] = W1[64][4], b1[64], W2[64][64], b2[64], W3[3][64], b3[3].
+ * X: dev float [n][4] features.  out: dev float [n][3] =
+ *   (sigma_scale softplus(o0), 1 + softplus(o1), alpha_scale softplus(o2)).
+ * act: dev float [n][131] saved activations (h1[64], h2[64], o[3]).
+ * All three enqueue on `stream` (cudaStream_t, NULL = default); n <= 1024. */
+int fdtd_mlp_forward(const float *theta, const float *X, int n, float sigma_scale,
+                     float alpha_scale, float *out, float *act, void *stream);
+/* gtheta (dev float [4675]) = dJ/dtheta from gout (dev float [n][3]). */
+int fdtd_mlp_backward(const float *theta, const float *X, int n, const float *act,
+                      const float *gout, float sigma_scale, float alpha_scale,
+                      float *gtheta, void *stream);
+/* Adam (Kingma & Ba) on nparam values; step t >= 1. */
+int fdtd_adam_step(float *theta, const float *grad, float *m, float *v, int nparam, int t,
+                   float lr, float beta1, float beta2, float eps, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDTD_H */
