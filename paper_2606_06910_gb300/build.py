@@ -51,14 +51,19 @@ def is_stale() -> bool:
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link libfdtd.so if it is missing or older than its sources."""
-    if not force and not is_stale():
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str | None = None) -> str:
+    """Compile and link libfdtd.so if it is missing or older than its sources.
+    ``out`` writes the library (and its objects) elsewhere, e.g. to compare
+    builds with different ``extra_flags``."""
+    lib_path = out or LIB
+    if out is None and not force and not is_stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    obj_dir = os.path.dirname(lib_path) if out else BUILD
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
     srcs = _sources()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    tag = os.path.basename(lib_path).replace(".so", "") if out else ""
+    objs = [os.path.join(obj_dir, tag + os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(args):
         src, obj = args
@@ -74,13 +79,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         list(ex.map(compile_one, zip(srcs, objs)))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -45,7 +45,7 @@ __device__ __forceinline__ float lam_h(const AdjArgs &A, int d, int z, int y, in
     if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz)
         return 0.f;
     const long long o = (long long)z * g.plane + (long long)y * g.nxp + x;
-    const float q = -A.kdt[o] * ap[o];
+    const float q = A.kdt[o] * ap[o];   // kdt holds -dt K / vscale
     const int k = axis_coord(d, z, y, x);
     if (in_slab(k, axis_len(g, d), g.lo[d], g.hi[d]))
         return A.ck[d][k] * q + A.ca[d][k] * (apsip_in[slab_index(g, d, z, y, x)] + q);
@@ -79,7 +79,7 @@ __global__ void adj_stage_a_kernel(AdjArgs A)
     const float *ap = A.ap + fo;
     const float lp = ap[o];
     A.gradK[fo + o] += -A.dt_over_vs * A.s_tape[fo + o] * lp;
-    const float q = -A.kdt[o] * lp;
+    const float q = A.kdt[o] * lp;
     const int dz[3] = {0, 0, 1}, dy[3] = {0, 1, 0}, dx[3] = {1, 0, 0};
     for (int d = 0; d < 3; ++d) {
         const float *psin = A.apsip_in[d] + (long long)shot * g.slab[d];
@@ -164,7 +164,7 @@ __global__ void grad_vel_kernel(const float *gradK, const float *kdt, Geom g, in
         double acc = 0.0;
         for (int s = 0; s < nshots; ++s)
             acc += gradK[(long long)s * g.vol + o];
-        const double c = sqrt((double)kdt[o] * vs_over_dt);   // K = rho c^2, rho = 1
+        const double c = sqrt(-(double)kdt[o] * vs_over_dt);   // K = rho c^2, rho = 1
         grad_vel[i] += (float)(2.0 * c * acc);
     }
 }

@@ -88,6 +88,8 @@ const char *check_desc(const fdtd_desc *d)
         const int lo = d->cpml_cells[2 * a], hi = d->cpml_cells[2 * a + 1];
         if (lo < 0 || hi < 0 || lo + hi > n[a])
             return "CPML cells must be >= 0 and fit inside their axis";
+        if (a == 0 && lo + hi > 0 && n[a] - lo - hi < 4)
+            return "the x interior between CPML layers must be at least 4 nodes wide";
     }
     if (d->storage != FDTD_F32 && d->storage != FDTD_F16 && d->storage != FDTD_BF16)
         return "unknown storage";
@@ -120,6 +122,7 @@ void make_layout(const fdtd_desc *d, Layout *L)
         g.hi[a] = d->cpml_cells[2 * a + 1];
         g.w[a] = g.lo[a] + g.hi[a];
     }
+    x_slab_layout(g.nx, g.lo[0], g.hi[0], &g.xhi, &g.w[0]);
     g.slab[0] = (long long)g.nz * g.ny * g.w[0];
     g.slab[1] = (long long)g.nz * g.w[1] * g.nxp;
     g.slab[2] = (long long)g.w[2] * g.ny * g.nxp;
@@ -256,8 +259,11 @@ void choose_zchunk(fdtd_ctx *c)
         const int kk = (nz + zc - 1) / zc;
         const long long ctas = per_z * kk;
         const long long waves = (ctas + slots - 1) / slots;
-        const double fill = (double)ctas / (double)(waves * slots);
-        const double eff = fill * (double)zc / (double)(zc + 4);
+        // time ~ waves x (planes + prologue); the 8 prologue iterations of a
+        // chunk cost about a third of a full plane each
+        const double eff = (double)nz * per_z / (double)slots / ((double)waves * (zc + 3.0));
+        if (zc < 16 && k > 1)
+            continue;
         if (eff > best_eff + 1e-9) {
             best_eff = eff;
             best = zc;

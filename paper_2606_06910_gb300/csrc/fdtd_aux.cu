@@ -7,7 +7,7 @@
 namespace fdtd {
 
 // ---------------------------------------------------------------------------
-// model: kdt = dt K / vscale with K = rho c^2 (rho = 1); min / max / invalid
+// model: kdt = -dt K / vscale with K = rho c^2 (rho = 1); min / max / invalid
 // ---------------------------------------------------------------------------
 __global__ void model_kernel(const float *__restrict__ vel, float *__restrict__ kdt, Geom g, double dt_over_vs,
                              unsigned *minmax)
@@ -28,7 +28,7 @@ __global__ void model_kernel(const float *__restrict__ vel, float *__restrict__ 
             kdt[i] = 0.f;
             continue;
         }
-        kdt[i] = (float)(dt_over_vs * (double)c * (double)c);
+        kdt[i] = (float)(-dt_over_vs * (double)c * (double)c);
         const unsigned b = __float_as_uint(c);   // positive floats order like unsigned ints
         vmin = min(vmin, b);
         vmax = max(vmax, b);

@@ -14,8 +14,8 @@ namespace fdtd {
 
 // Forward tile: TX x TY nodes in (x, y) per CTA, each thread owns 4
 // consecutive x nodes of one row; the CTA marches a z range.
-constexpr int TX = 64;
-constexpr int TY = 16;
+constexpr int TX = 32;
+constexpr int TY = 32;
 constexpr int NTHREADS = (TX / 4) * TY;   // 256
 constexpr int NSTAGE = 3;                 // TMA pipeline depth (planes in flight)
 
@@ -194,6 +194,12 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// bring the line holding p into L2 (no register result, no wait)
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
@@ -202,33 +208,63 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
 // ---------------------------------------------------------------------------
 // geometry shared by kernels and host
 // ---------------------------------------------------------------------------
+// Memory variables live only in their slabs.  y and z slabs are whole rows /
+// planes: [nz][lo+hi][nxp] and [lo+hi][ny][nxp].  The x slabs are short row
+// segments: [nz][ny][w0] with the low face at compact x = x and the high face
+// at compact x = xhi + (x - (nx - hi)), where xhi keeps compact x congruent to
+// x modulo 4 (16-byte vectors of 4 nodes stay aligned) and leaves at least 4
+// unused entries between the faces and after the high face, so a vector that
+// straddles a slab edge reads or writes only padding outside the slab.
 struct Geom {
     int nx, ny, nz, nxp;     // nodes, padded row pitch (elements, multiple of 8)
     long long plane;         // ny * nxp
     long long vol;           // nz * plane (elements per shot)
     int lo[3], hi[3];        // CPML cells per axis (x, y, z)
-    int w[3];                // lo + hi
+    int w[3];                // compact width: w0 padded (see above), w1 = lo+hi, w2 = lo+hi
+    int xhi;                 // compact x of the first high-face node
     long long slab[3];       // memory-variable elements per shot and axis
 };
-
-// compact index of node (z, y, x) in the memory-variable array of axis d
-__host__ __device__ __forceinline__ int slab_coord(int i, int n, int lo, int hi)
-{
-    return i < lo ? i : lo + (i - (n - hi));
-}
 
 __host__ __device__ __forceinline__ bool in_slab(int i, int n, int lo, int hi)
 {
     return i < lo || i >= n - hi;
 }
 
+// compact coordinate along the slab axis (y or z: rows / planes of the slab)
+__host__ __device__ __forceinline__ int slab_coord(int i, int n, int lo, int hi)
+{
+    return i < lo ? i : lo + (i - (n - hi));
+}
+
+// compact x of node x in [0, nx + 3): the 4-vector starting at x & ~3 maps
+// with the low face if it starts inside the low face, else with the high face
+// (the x interior is at least 4 nodes wide, so no vector touches both faces)
+__host__ __device__ __forceinline__ int slab_x(const Geom &g, int x)
+{
+    return (x & ~3) < g.lo[0] ? x : g.xhi + (x - (g.nx - g.hi[0]));
+}
+
 __host__ __device__ __forceinline__ long long slab_index(const Geom &g, int d, int z, int y, int x)
 {
     if (d == 0)
-        return ((long long)z * g.ny + y) * g.w[0] + slab_coord(x, g.nx, g.lo[0], g.hi[0]);
+        return ((long long)z * g.ny + y) * g.w[0] + slab_x(g, x);
     if (d == 1)
         return ((long long)z * g.w[1] + slab_coord(y, g.ny, g.lo[1], g.hi[1])) * g.nxp + x;
     return ((long long)slab_coord(z, g.nz, g.lo[2], g.hi[2]) * g.ny + y) * g.nxp + x;
+}
+
+// x-slab layout for a grid with nx nodes and lo / hi cells (host and tests)
+__host__ __device__ __forceinline__ void x_slab_layout(int nx, int lo, int hi, int *xhi, int *w0)
+{
+    if (lo + hi == 0) {
+        *xhi = 0;
+        *w0 = 0;
+        return;
+    }
+    const int base = (lo + 3) / 4 * 4 + 4;                 // low face + >= 4 padding
+    const int r = ((nx - hi) % 4 + 4) % 4;                 // xhi == nx - hi (mod 4)
+    *xhi = base + ((r - base % 4) + 4) % 4;
+    *w0 = (*xhi + hi + 3) / 4 * 4 + 4;                     // high face + >= 4 padding
 }
 
 // Arguments of the fused forward step kernel (one launch = one time step).
@@ -278,7 +314,7 @@ struct fdtd_ctx {
     unsigned char *ws;
     size_t ws_bytes;
     void *p[2], *v[3][2], *psiv[3][2], *psip[3];
-    float *kdt;             // dt K / vscale per node [nz][ny][nxp]
+    float *kdt;             // -dt K / vscale per node [nz][ny][nxp] (0 in the row padding)
     float *coef;            // [3][3][nmax]: b, a, 1/kappa per axis and node
     float *wavelet;         // [nshots][nt_max]
     int nt_w;

@@ -13,7 +13,23 @@
 // reads p, v, K once and writes p, v once (36 B per node for FP32).
 // The inputs of plane t arrive through a 3-deep TMA/mbarrier pipeline; TMA
 // out-of-bounds fill supplies the zero values beyond the grid.
+//
+// Arithmetic is FP32 in registers, packed two nodes per instruction
+// (FFMA2/FMUL2/FADD2).  In the CPML slabs the memory variables of the next
+// plane are prefetched into L2 one plane ahead; the CPML update is the same
+// vector formula everywhere, since the coefficient tables hold b = a = 0,
+// 1/kappa = 1 outside the slabs.
 #include "fdtd_internal.cuh"
+
+#ifndef FDTD_PACKED
+#define FDTD_PACKED 1
+#endif
+#ifndef FDTD_MINB
+#define FDTD_MINB 2
+#endif
+#ifndef FDTD_PREFETCH
+#define FDTD_PREFETCH 1
+#endif
 
 namespace fdtd {
 
@@ -39,103 +55,162 @@ struct StageLayout {
     static_assert(OFF_PQ % 128 == 0 && OFF_VX % 128 == 0 && OFF_VY % 128 == 0 && OFF_VZ % 128 == 0 &&
                       OFF_K % 128 == 0 && BYTES % 128 == 0,
                   "TMA destinations must stay 128-byte aligned");
-    static constexpr int SVX_FLOATS = TY * (TX + 8);   // v'_x, origin x0 - 4
+    static constexpr int SVXW = TX + 8;                // v'_x row, origin x0 - 4
+    static constexpr int SVX_FLOATS = TY * SVXW;
     static constexpr int SVY_FLOATS = (TY + 8) * TX;   // v'_y, origin y0 - 4
     static constexpr int SMEM = NSTAGE * BYTES + 4 * (SVX_FLOATS + SVY_FLOATS) + 8 * NSTAGE;
 };
 
-__device__ __forceinline__ F4 f4zero() { return F4{{0.f, 0.f, 0.f, 0.f}}; }
+// four consecutive x nodes as two packed pairs
+struct V4 {
+    float2 a, b;
+};
 
-// centred radius-4 derivative of 4 consecutive outputs from the 12 values at
-// offsets -4..7 (a, b, c hold offsets -4..-1, 0..3, 4..7)
-__device__ __forceinline__ F4 dx4(const F4 &a, const F4 &b, const F4 &c, const float *cw)
+__device__ __forceinline__ V4 v4zero() { return V4{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+__device__ __forceinline__ V4 to_v4(const F4 &f) { return V4{make_float2(f.v[0], f.v[1]), make_float2(f.v[2], f.v[3])}; }
+__device__ __forceinline__ F4 to_f4(const V4 &v) { return F4{{v.a.x, v.a.y, v.b.x, v.b.y}}; }
+#if FDTD_PACKED
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+#else
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
 {
-    float f[12] = {a.v[0], a.v[1], a.v[2], a.v[3], b.v[0], b.v[1], b.v[2], b.v[3], c.v[0], c.v[1], c.v[2], c.v[3]};
-    F4 r;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        r.v[i] = cw[0] * (f[i + 5] - f[i + 3]) + cw[1] * (f[i + 6] - f[i + 2]) + cw[2] * (f[i + 7] - f[i + 1]) +
-                 cw[3] * (f[i + 8] - f[i]);
-    return r;
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
 }
-
-// centred derivative from 8 neighbours: m[l-1] = f(-l), p[l-1] = f(+l)
-__device__ __forceinline__ F4 dn4(const F4 *m, const F4 *p, const float *cw)
-{
-    F4 r;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        r.v[i] = cw[0] * (p[0].v[i] - m[0].v[i]) + cw[1] * (p[1].v[i] - m[1].v[i]) +
-                 cw[2] * (p[2].v[i] - m[2].v[i]) + cw[3] * (p[3].v[i] - m[3].v[i]);
-    return r;
-}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+#endif
+__device__ __forceinline__ V4 fma4(float2 s, const V4 &x, const V4 &y) { return V4{fma2(s, x.a, y.a), fma2(s, x.b, y.b)}; }
+__device__ __forceinline__ V4 mul4(const V4 &x, const V4 &y) { return V4{mul2(x.a, y.a), mul2(x.b, y.b)}; }
+__device__ __forceinline__ V4 add4(const V4 &x, const V4 &y) { return V4{add2(x.a, y.a), add2(x.b, y.b)}; }
 
 template <typename T>
-__device__ __forceinline__ F4 lds4(const unsigned char *base, int elem)
+__device__ __forceinline__ V4 lds(const unsigned char *base, int elem)
 {
-    return Io<T>::ld4(reinterpret_cast<const T *>(base) + elem);
+    return to_v4(Io<T>::ld4(reinterpret_cast<const T *>(base) + elem));
 }
 
-__device__ __forceinline__ F4 lds4f(const float *p)
+__device__ __forceinline__ V4 ldsf(const float *p)
 {
     float4 q = *reinterpret_cast<const float4 *>(p);
-    return F4{{q.x, q.y, q.z, q.w}};
+    return V4{make_float2(q.x, q.y), make_float2(q.z, q.w)};
 }
 
-__device__ __forceinline__ void sts4f(float *p, const F4 &v)
+__device__ __forceinline__ void stsf(float *p, const V4 &v)
 {
-    *reinterpret_cast<float4 *>(p) = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
+    *reinterpret_cast<float4 *>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
 }
 
-// x-direction CPML on 4 consecutive nodes starting at gx (row y, plane z):
-// psi <- b psi + a g ; g <- kinv g + psi.  Reads psi from `pin`, writes to
-// `pout` when write is set (pout may equal pin).  Optionally tapes (g, psi_old).
-template <typename T>
-__device__ __forceinline__ void cpml_x(const Geom &G, const StepArgs &A, F4 &gv, const T *pin, T *pout,
-                                       int z, int y, int gx, bool write, float *tape, int tape_off)
+// Coefficients a_l / h as packed pairs: cp = (c, c), cn = (-c, -c).
+struct Coef {
+    float2 cp[4], cn[4];
+};
+
+// centred derivative from aligned neighbours: m[l-1] = f(-l), p[l-1] = f(+l)
+__device__ __forceinline__ V4 dnb(const V4 *m, const V4 *p, const Coef &C)
 {
+    V4 r;
+    r.a = mul2(C.cp[0], p[0].a);
+    r.b = mul2(C.cp[0], p[0].b);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int x = gx + i;
-        if (x < G.nx && in_slab(x, G.nx, G.lo[0], G.hi[0])) {
-            long long idx = ((long long)z * G.ny + y) * G.w[0] + slab_coord(x, G.nx, G.lo[0], G.hi[0]);
-            float ps = Io<T>::ld1(pin + idx);
-            float b = __ldg(A.cb[0] + x), a = __ldg(A.ca[0] + x), k = __ldg(A.ck[0] + x);
-            float pn = b * ps + a * gv.v[i];
-            if (tape) {
-                tape[idx * 4 + tape_off] = gv.v[i];
-                tape[idx * 4 + tape_off + 1] = ps;
-            }
-            gv.v[i] = k * gv.v[i] + pn;
-            if (write)
-                Io<T>::st1(pout + idx, pn);
+    for (int l = 0; l < 4; ++l) {
+        if (l > 0) {
+            r.a = fma2(C.cp[l], p[l].a, r.a);
+            r.b = fma2(C.cp[l], p[l].b, r.b);
         }
+        r.a = fma2(C.cn[l], m[l].a, r.a);
+        r.b = fma2(C.cn[l], m[l].b, r.b);
+    }
+    return r;
+}
+
+// x derivative of 4 consecutive outputs from the 12 values at offsets -4..7
+// (u, v, w hold offsets -4..-1, 0..3, 4..7).  Even offsets pair up with the
+// packed layout; odd offsets use scalar FMAs on the same accumulators.
+__device__ __forceinline__ V4 dx4(const V4 &u, const V4 &v, const V4 &w, const Coef &C)
+{
+    const float f[12] = {u.a.x, u.a.y, u.b.x, u.b.y, v.a.x, v.a.y, v.b.x, v.b.y, w.a.x, w.a.y, w.b.x, w.b.y};
+    // packed pairs P[k] = (f[2k], f[2k+1])
+    const float2 P0 = u.a, P1 = u.b, P2 = v.a, P3 = v.b, P4 = w.a, P5 = w.b;
+    V4 r;
+    // l = 2, 4 (aligned): pair (o0,o1) centred at f4,f5; pair (o2,o3) at f6,f7
+    r.a = mul2(C.cp[1], P3);
+    r.a = fma2(C.cn[1], P1, r.a);
+    r.a = fma2(C.cp[3], P4, r.a);
+    r.a = fma2(C.cn[3], P0, r.a);
+    r.b = mul2(C.cp[1], P4);
+    r.b = fma2(C.cn[1], P2, r.b);
+    r.b = fma2(C.cp[3], P5, r.b);
+    r.b = fma2(C.cn[3], P1, r.b);
+    // l = 1, 3 (odd offsets), scalar
+    const float c1 = C.cp[0].x, c3 = C.cp[2].x;
+    r.a.x = fmaf(c1, f[5] - f[3], r.a.x);
+    r.a.y = fmaf(c1, f[6] - f[4], r.a.y);
+    r.b.x = fmaf(c1, f[7] - f[5], r.b.x);
+    r.b.y = fmaf(c1, f[8] - f[6], r.b.y);
+    r.a.x = fmaf(c3, f[7] - f[1], r.a.x);
+    r.a.y = fmaf(c3, f[8] - f[2], r.a.y);
+    r.b.x = fmaf(c3, f[9] - f[3], r.b.x);
+    r.b.y = fmaf(c3, f[10] - f[4], r.b.y);
+    return r;
+}
+
+// One CPML update of 4 nodes: psi' = b psi + a g ; g' = kinv g + psi'.
+__device__ __forceinline__ V4 cpml4(V4 &g, const V4 &psi, const V4 &b, const V4 &a, const V4 &k)
+{
+    V4 pn;
+    pn.a = fma2(b.a, psi.a, mul2(a.a, g.a));
+    pn.b = fma2(b.b, psi.b, mul2(a.b, g.b));
+    g.a = fma2(k.a, g.a, pn.a);
+    g.b = fma2(k.b, g.b, pn.b);
+    return pn;
+}
+
+__device__ __forceinline__ V4 splat4(float s) { return V4{make_float2(s, s), make_float2(s, s)}; }
+
+template <typename T>
+__device__ __forceinline__ V4 ldg_v4(const T *p) { return to_v4(Io<T>::ld4(p)); }
+
+// tape (g, psi_old) of 4 nodes into slots [idx*4 + off, +1]
+__device__ __forceinline__ void tape4(float *tape, long long idx, int off, const V4 &g, const V4 &psi)
+{
+    const F4 gf = to_f4(g), pf = to_f4(psi);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float2 *>(tape + (idx + i) * 4 + off) = make_float2(gf.v[i], pf.v[i]);
+}
+
+// Queue work of one plane.  Logical entry j of each 9-deep queue lives in
+// slot j: pq[j] = p(t + j), vzq[j] = v'_z(t - 4 + j); the queues shift by one
+// slot per plane.
+template <typename Zvel>
+__device__ __forceinline__ void zblock(V4 (&pq)[9], V4 (&vzq)[9], const V4 &pnew, const Coef &C, Zvel &&zvel,
+                                       V4 &pt, V4 &hz)
+{
+    pq[8] = pnew;
+    V4 gz;
+    {
+        const V4 m[4] = {pq[3], pq[2], pq[1], pq[0]};
+        const V4 p[4] = {pq[5], pq[6], pq[7], pq[8]};
+        gz = dnb(m, p, C);
+    }
+    pt = pq[0];
+    vzq[8] = zvel(gz);
+    {
+        const V4 m[4] = {vzq[3], vzq[2], vzq[1], vzq[0]};
+        const V4 p[4] = {vzq[5], vzq[6], vzq[7], vzq[8]};
+        hz = dnb(m, p, C);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        pq[k] = pq[k + 1];
+        vzq[k] = vzq[k + 1];
     }
 }
 
-// y- or z-direction CPML: the 4 nodes share one profile value and are
-// contiguous in the memory-variable array.
 template <typename T>
-__device__ __forceinline__ void cpml_yz(F4 &gv, const T *pin, T *pout, long long idx, float b, float a, float k,
-                                        bool write, int nvalid, float *tape, int tape_off)
-{
-    F4 ps = Io<T>::ld4(pin + idx);
-    F4 pn;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        pn.v[i] = b * ps.v[i] + a * gv.v[i];
-        if (tape && i < nvalid) {
-            tape[(idx + i) * 4 + tape_off] = gv.v[i];
-            tape[(idx + i) * 4 + tape_off + 1] = ps.v[i];
-        }
-        gv.v[i] = k * gv.v[i] + pn.v[i];
-    }
-    if (write)
-        Io<T>::st4(pout + idx, pn);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(NTHREADS, 2)
+__global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
     fdtd_step_kernel(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mPq,
                      const __grid_constant__ CUtensorMap mVX, const __grid_constant__ CUtensorMap mVY,
                      const __grid_constant__ CUtensorMap mVZ, const __grid_constant__ CUtensorMap mK,
@@ -146,6 +221,10 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     float *svx = reinterpret_cast<float *>(smem + NSTAGE * L::BYTES);
     float *svy = svx + L::SVX_FLOATS;
     uint64_t *bar = reinterpret_cast<uint64_t *>(svy + L::SVY_FLOATS);
+    // CPML coefficients (b, a, 1/kappa) of the tile's x range [x0-4, x0+TX+4)
+    // and y range [y0-4, y0+TY+4); 0, 0, 1 outside the slabs and the grid
+    __shared__ __align__(16) float sCx[3][TX + 8];
+    __shared__ __align__(16) float sCy[3][TY + 8];
 
     const Geom &G = A.g;
     const int tid = threadIdx.x;
@@ -157,11 +236,17 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     const int shot = blockIdx.z;
     const int gx = x0 + 4 * tx, gy = y0 + ty;
     const int niter = z1 - z0 + 8;
-    const float cw[4] = {A.c[0], A.c[1], A.c[2], A.c[3]};
+
+    Coef C;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        C.cp[l] = make_float2(A.c[l], A.c[l]);
+        C.cn[l] = make_float2(-A.c[l], -A.c[l]);
+    }
+    const float2 ndtr = make_float2(-A.dtr, -A.dtr);
 
     const long long fofs = (long long)shot * G.vol;
     const T *p_in = reinterpret_cast<const T *>(A.p_in) + fofs;
-    T *p_out = reinterpret_cast<T *>(A.p_out) + fofs;
     T *v_out[3];
     const T *psiv_in[3];
     T *psiv_out[3], *psip[3];
@@ -177,20 +262,53 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     for (int d = 0; d < 3; ++d)
         stape[d] = A.slab_tape[d] ? A.slab_tape[d] + (long long)shot * G.slab[d] * 4 : nullptr;
 
-    // which of this thread's 4 own nodes lie inside the grid
-    bool own_ok[4];
-    int nvalid = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        own_ok[i] = (gx + i < G.nx) && (gy < G.ny);
-        nvalid += own_ok[i] ? 1 : 0;
+    for (int i = tid; i < 3 * (TX + 8); i += NTHREADS) {
+        const int c = i / (TX + 8), x = x0 - 4 + i % (TX + 8);
+        const bool in = x >= 0 && x < G.nx && in_slab(x, G.nx, G.lo[0], G.hi[0]);
+        sCx[c][i % (TX + 8)] = in ? (c == 0 ? A.cb[0][x] : (c == 1 ? A.ca[0][x] : A.ck[0][x])) : (c == 2 ? 1.f : 0.f);
     }
+    for (int i = tid; i < 3 * (TY + 8); i += NTHREADS) {
+        const int c = i / (TY + 8), y = y0 - 4 + i % (TY + 8);
+        const bool in = y >= 0 && y < G.ny && in_slab(y, G.ny, G.lo[1], G.hi[1]);
+        sCy[c][i % (TY + 8)] = in ? (c == 0 ? A.cb[1][y] : (c == 1 ? A.ca[1][y] : A.ck[1][y])) : (c == 2 ? 1.f : 0.f);
+    }
+
+    // validity of the 4 own nodes (ghost nodes beyond the grid hold 0)
     const bool row_ok = gy < G.ny && gx < G.nxp;
+    float mk[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        mk[i] = ((gx + i < G.nx) && (gy < G.ny)) ? 1.f : 0.f;
+    const V4 mask = V4{make_float2(mk[0], mk[1]), make_float2(mk[2], mk[3])};
+    const bool full_tile = (x0 + TX <= G.nx) && (y0 + TY <= G.ny);
+    const long long rowofs = (long long)gy * G.nxp + gx;
+
+    // which memory variables this thread touches (own vector, halo vector)
+    const bool own_x = G.w[0] > 0 && gy < G.ny && gx < G.nx && (gx < G.lo[0] || gx + 3 >= G.nx - G.hi[0]);
+    const bool own_y = G.w[1] > 0 && row_ok && in_slab(gy, G.ny, G.lo[1], G.hi[1]);
+
+    // halo task of this thread (warps 4-5: y halo rows, warps 6-7: x halo)
+    const int hy_task = tid - NTHREADS / 2;
+    const int hx_task = tid - (NTHREADS / 2 + 8 * (TX / 4));
+    const bool do_yhalo = hy_task >= 0 && hy_task < 8 * (TX / 4);
+    const bool do_xhalo = hx_task >= 0 && hx_task < 2 * TY;
+    const int yh_r = do_yhalo ? hy_task / (TX / 4) : 0, yh_c = do_yhalo ? hy_task % (TX / 4) : 0;
+    const int yh_y = yh_r < 4 ? y0 - 4 + yh_r : y0 + TY + (yh_r - 4);
+    const int yh_x = x0 + 4 * yh_c;
+    const int xh_r = do_xhalo ? (hx_task >> 1) : 0;
+    const int xh_x = (do_xhalo && (hx_task & 1)) ? x0 + TX : x0 - 4;
+    const int xh_y = y0 + xh_r;
+    const bool yh_in = yh_y >= 0 && yh_y < G.ny;
+    const bool halo_psi_y = do_yhalo && G.w[1] > 0 && yh_in && yh_x < G.nxp && in_slab(yh_y, G.ny, G.lo[1], G.hi[1]);
+    const bool halo_psi_x = do_xhalo && G.w[0] > 0 && xh_y < G.ny && xh_x >= 0 && xh_x < G.nx &&
+                            (xh_x < G.lo[0] || xh_x + 3 >= G.nx - G.hi[0]);
+    const bool slab_thread = own_x || own_y || halo_psi_x || halo_psi_y;
 
     // source of this shot
     const int sz = A.src ? A.src[3 * shot] : -1, sy = A.src ? A.src[3 * shot + 1] : -1,
               sx = A.src ? A.src[3 * shot + 2] : -1;
     const float wsrc = (A.src && A.t < A.nt_w) ? A.wavelet[(long long)shot * A.nt_w + A.t] : 0.f;
+    const bool src_here = A.src && sy == gy && sx >= gx && sx < gx + 4 && sz >= z0 && sz < z1;
     // receivers of this tile (sorted by z)
     int rc = 0, r1 = 0;
     const bool rec_on = A.traces != nullptr && A.nrec > 0 && A.t < A.nt_max;
@@ -240,150 +358,175 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         for (int i = 0; i < NSTAGE && i < niter; ++i)
             issue(i);
 
-    // register queues: pq[k] = p(t + k), vzq[k] = v'_z(t - 4 + k)
-    F4 pq[9], vzq[9];
+    // register queues: pq[j] = p(t + j), vzq[j] = v'_z(t - 4 + j)
+    V4 pq[9], vzq[9];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int z = z0 - 8 + k;
-        pq[k] = f4zero();
-        if (z >= 0 && row_ok) {
-            F4 q = Io<T>::ldg4(p_in + (long long)z * G.plane + (long long)gy * G.nxp + gx);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                pq[k].v[i] = own_ok[i] ? q.v[i] : 0.f;
-        }
-        vzq[k] = f4zero();
+        pq[k] = v4zero();
+        if (z >= 0 && row_ok)
+            pq[k] = to_v4(Io<T>::ldg4(p_in + (long long)z * G.plane + rowofs));
+        vzq[k] = v4zero();
     }
-    pq[8] = f4zero();
-    vzq[8] = f4zero();
+    pq[8] = v4zero();
+    vzq[8] = v4zero();
 
     for (int it = 0; it < niter; ++it) {
         const int t = z0 - 8 + it;
+        const int zv = t + 4;
+        const bool active = t >= z0;
         const unsigned char *S = smem + (it % NSTAGE) * L::BYTES;
+
+        const bool zs_v = row_ok && zv >= 0 && zv < G.nz && in_slab(zv, G.nz, G.lo[2], G.hi[2]);
+        const bool zs_p = active && row_ok && in_slab(t, G.nz, G.lo[2], G.hi[2]);
+
+        // L2 prefetch of the memory variables of the next plane, so that the
+        // slab loads of the next iteration do not wait on HBM
+        if (FDTD_PREFETCH) {
+            const int tn = t + 1, zn = zv + 1;
+            if (row_ok && zn < G.nz && zn >= 0 && in_slab(zn, G.nz, G.lo[2], G.hi[2]))
+                prefetch_l2(psiv_in[2] + slab_index(G, 2, zn, gy, gx));
+            if (tn >= z0 && tn < z1) {
+                if (row_ok && in_slab(tn, G.nz, G.lo[2], G.hi[2]))
+                    prefetch_l2(psip[2] + slab_index(G, 2, tn, gy, gx));
+                if (slab_thread) {
+                    if (own_x) {
+                        const long long i = slab_index(G, 0, tn, gy, gx);
+                        prefetch_l2(psiv_in[0] + i);
+                        prefetch_l2(psip[0] + i);
+                    }
+                    if (own_y) {
+                        const long long i = slab_index(G, 1, tn, gy, gx);
+                        prefetch_l2(psiv_in[1] + i);
+                        prefetch_l2(psip[1] + i);
+                    }
+                    if (halo_psi_y)
+                        prefetch_l2(psiv_in[1] + slab_index(G, 1, tn, yh_y, yh_x));
+                    if (halo_psi_x)
+                        prefetch_l2(psiv_in[0] + slab_index(G, 0, tn, xh_y, xh_x));
+                }
+            }
+        }
+
         const bool ok = mbar_wait_bounded(&bar[it % NSTAGE], (it / NSTAGE) & 1, WAIT_LIMIT);
 
-        // ---- p(t + 8) into the queue
-        pq[8] = f4zero();
-        if (ok && t + 8 < G.nz) {
-            F4 q = lds4<T>(S + L::OFF_PQ, ty * TX + 4 * tx);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                pq[8].v[i] = own_ok[i] ? q.v[i] : 0.f;
-        }
-
-        // ---- v'_z at plane t + 4 (velocity half step, z component)
-        const int zv = t + 4;
-        F4 vzn = f4zero();
-        if (ok && zv >= 0 && zv < G.nz) {
-            F4 gz;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                gz.v[i] = cw[0] * (pq[5].v[i] - pq[3].v[i]) + cw[1] * (pq[6].v[i] - pq[2].v[i]) +
-                          cw[2] * (pq[7].v[i] - pq[1].v[i]) + cw[3] * (pq[8].v[i] - pq[0].v[i]);
-            const bool owned = zv >= z0 && zv < z1;
-            if (row_ok && in_slab(zv, G.nz, G.lo[2], G.hi[2])) {
-                const long long idx = slab_index(G, 2, zv, gy, gx);
-                cpml_yz<T>(gz, psiv_in[2], psiv_out[2], idx, __ldg(A.cb[2] + zv), __ldg(A.ca[2] + zv),
-                           __ldg(A.ck[2] + zv), owned, nvalid, owned ? stape[2] : nullptr, 0);
+        // ---- z block: p(t + 8) into the queue (TMA zero-fills nodes beyond the
+        // grid), D_z p and v'_z at plane t + 4, D_z v'_z at plane t, and p(t)
+        const V4 pnew = (ok && t + 8 < G.nz) ? lds<T>(S + L::OFF_PQ, ty * TX + 4 * tx) : v4zero();
+        auto zvel = [&](V4 gz) -> V4 {
+            V4 vzn = v4zero();
+            if (ok && zv >= 0 && zv < G.nz) {
+                const bool owned = zv >= z0 && zv < z1;
+                if (zs_v) {
+                    const long long izv = slab_index(G, 2, zv, gy, gx);
+                    const V4 psvz = ldg_v4(psiv_in[2] + izv);
+                    const V4 b = splat4(__ldg(A.cb[2] + zv)), a = splat4(__ldg(A.ca[2] + zv)),
+                             k = splat4(__ldg(A.ck[2] + zv));
+                    if (owned && stape[2])
+                        tape4(stape[2], izv, 0, gz, psvz);
+                    const V4 pn = cpml4(gz, psvz, b, a, k);
+                    if (owned)
+                        Io<T>::st4(psiv_out[2] + izv, to_f4(pn));
+                }
+                vzn = fma4(ndtr, gz, lds<T>(S + L::OFF_VZ, ty * TX + 4 * tx));
+                if (owned && row_ok)
+                    Io<T>::st4(v_out[2] + (long long)zv * G.plane + rowofs, to_f4(vzn));
             }
-            F4 vo = lds4<T>(S + L::OFF_VZ, ty * TX + 4 * tx);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                vzn.v[i] = own_ok[i] ? vo.v[i] - A.dtr * gz.v[i] : 0.f;
-            if (owned && row_ok)
-                Io<T>::st4(v_out[2] + (long long)zv * G.plane + (long long)gy * G.nxp + gx, vzn);
-        }
-        vzq[8] = vzn;
+            return vzn;
+        };
+        V4 pt, hz4;
+        zblock(pq, vzq, pnew, C, zvel, pt, hz4);
 
-        const bool active = t >= z0;
         if (ok && active) {
             const unsigned char *Sp = S + L::OFF_P;   // p plane, origin (x0 - 8, y0 - 8)
+            const long long pofs = (long long)t * G.plane + rowofs;
             // ---- v'_x, own nodes
             {
                 const int lrow = (ty + 8) * L::PW, lx = 4 * tx + 8;
-                F4 g = dx4(lds4<T>(Sp, lrow + lx - 4), lds4<T>(Sp, lrow + lx), lds4<T>(Sp, lrow + lx + 4), cw);
-                if (gy < G.ny && (gx < G.lo[0] || gx + 3 >= G.nx - G.hi[0]))
-                    cpml_x<T>(G, A, g, psiv_in[0], psiv_out[0], t, gy, gx, true, stape[0], 0);
-                F4 vo = lds4<T>(S + L::OFF_VX, ty * L::VXW + 4 * tx + 8);
-                F4 vn;
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    vn.v[i] = own_ok[i] ? vo.v[i] - A.dtr * g.v[i] : 0.f;
-                if (row_ok)
-                    Io<T>::st4(v_out[0] + (long long)t * G.plane + (long long)gy * G.nxp + gx, vn);
-                sts4f(svx + ty * (TX + 8) + 4 * tx + 4, vn);
-            }
-            // ---- v'_x, 4-node x halo on both sides (recomputed, not stored)
-            if (tid < 2 * TY) {
-                const int r = tid >> 1, side = tid & 1;
-                const int hx = side ? x0 + TX : x0 - 4;
-                const int hy = y0 + r;
-                const int lrow = (r + 8) * L::PW, lx = hx - x0 + 8;
-                F4 g = dx4(lds4<T>(Sp, lrow + lx - 4), lds4<T>(Sp, lrow + lx), lds4<T>(Sp, lrow + lx + 4), cw);
-                if (hy < G.ny && hx >= 0 && hx < G.nx)
-                    cpml_x<T>(G, A, g, psiv_in[0], psiv_out[0], t, hy, hx, false, nullptr, 0);
-                F4 vo = lds4<T>(S + L::OFF_VX, r * L::VXW + lx);
-                F4 vn;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const bool in = hy < G.ny && hx + i >= 0 && hx + i < G.nx;
-                    vn.v[i] = in ? vo.v[i] - A.dtr * g.v[i] : 0.f;
+                V4 g = dx4(lds<T>(Sp, lrow + lx - 4), lds<T>(Sp, lrow + lx), lds<T>(Sp, lrow + lx + 4), C);
+                if (own_x) {
+                    const int cx = 4 * tx + 4;
+                    const long long ix = slab_index(G, 0, t, gy, gx);
+                    const V4 psvx = ldg_v4(psiv_in[0] + ix);
+                    if (stape[0])
+                        tape4(stape[0], ix, 0, g, psvx);
+                    const V4 pn = cpml4(g, psvx, ldsf(&sCx[0][cx]), ldsf(&sCx[1][cx]), ldsf(&sCx[2][cx]));
+                    Io<T>::st4(psiv_out[0] + ix, to_f4(pn));
                 }
-                sts4f(svx + r * (TX + 8) + (hx - x0 + 4), vn);
+                V4 vn = fma4(ndtr, g, lds<T>(S + L::OFF_VX, ty * L::VXW + 4 * tx + 8));
+                if (!full_tile)
+                    vn = mul4(vn, mask);
+                if (row_ok)
+                    Io<T>::st4(v_out[0] + pofs, to_f4(vn));
+                stsf(svx + ty * L::SVXW + 4 * tx + 4, vn);
             }
             // ---- v'_y, own nodes
             {
                 const int lx = 4 * tx + 8, ly = ty + 8;
-                F4 m[4], p[4];
+                V4 m[4], p[4];
 #pragma unroll
                 for (int l = 1; l <= 4; ++l) {
-                    m[l - 1] = lds4<T>(Sp, (ly - l) * L::PW + lx);
-                    p[l - 1] = lds4<T>(Sp, (ly + l) * L::PW + lx);
+                    m[l - 1] = lds<T>(Sp, (ly - l) * L::PW + lx);
+                    p[l - 1] = lds<T>(Sp, (ly + l) * L::PW + lx);
                 }
-                F4 g = dn4(m, p, cw);
-                if (row_ok && in_slab(gy, G.ny, G.lo[1], G.hi[1])) {
-                    const long long idx = slab_index(G, 1, t, gy, gx);
-                    cpml_yz<T>(g, psiv_in[1], psiv_out[1], idx, __ldg(A.cb[1] + gy), __ldg(A.ca[1] + gy),
-                               __ldg(A.ck[1] + gy), true, nvalid, stape[1], 0);
+                V4 g = dnb(m, p, C);
+                if (own_y) {
+                    const long long iy = slab_index(G, 1, t, gy, gx);
+                    const V4 psvy = ldg_v4(psiv_in[1] + iy);
+                    if (stape[1])
+                        tape4(stape[1], iy, 0, g, psvy);
+                    const V4 pn = cpml4(g, psvy, splat4(sCy[0][ty + 4]), splat4(sCy[1][ty + 4]), splat4(sCy[2][ty + 4]));
+                    Io<T>::st4(psiv_out[1] + iy, to_f4(pn));
                 }
-                F4 vo = lds4<T>(S + L::OFF_VY, (ty + 4) * TX + 4 * tx);
-                F4 vn;
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    vn.v[i] = own_ok[i] ? vo.v[i] - A.dtr * g.v[i] : 0.f;
+                V4 vn = fma4(ndtr, g, lds<T>(S + L::OFF_VY, (ty + 4) * TX + 4 * tx));
+                if (!full_tile)
+                    vn = mul4(vn, mask);
                 if (row_ok)
-                    Io<T>::st4(v_out[1] + (long long)t * G.plane + (long long)gy * G.nxp + gx, vn);
-                sts4f(svy + (ty + 4) * TX + 4 * tx, vn);
+                    Io<T>::st4(v_out[1] + pofs, to_f4(vn));
+                stsf(svy + (ty + 4) * TX + 4 * tx, vn);
             }
-            // ---- v'_y, 4-row y halo above and below (recomputed, not stored)
-            for (int hsk = tid; hsk < 8 * (TX / 4); hsk += NTHREADS) {
-                const int r = hsk / (TX / 4), c = hsk % (TX / 4);
-                const int hy = r < 4 ? y0 - 4 + r : y0 + TY + (r - 4);
-                const int hx = x0 + 4 * c;
-                const int ly = hy - y0 + 8, lx = 4 * c + 8;
-                F4 m[4], p[4];
+            // ---- halos (recomputed, not stored)
+            if (do_yhalo) {
+                const int ly = yh_y - y0 + 8, lx = 4 * yh_c + 8;
+                V4 m[4], p[4];
 #pragma unroll
                 for (int l = 1; l <= 4; ++l) {
-                    m[l - 1] = lds4<T>(Sp, (ly - l) * L::PW + lx);
-                    p[l - 1] = lds4<T>(Sp, (ly + l) * L::PW + lx);
+                    m[l - 1] = lds<T>(Sp, (ly - l) * L::PW + lx);
+                    p[l - 1] = lds<T>(Sp, (ly + l) * L::PW + lx);
                 }
-                F4 g = dn4(m, p, cw);
-                const bool yin = hy >= 0 && hy < G.ny;
-                if (yin && hx < G.nxp && in_slab(hy, G.ny, G.lo[1], G.hi[1])) {
-                    const long long idx = slab_index(G, 1, t, hy, hx);
-                    cpml_yz<T>(g, psiv_in[1], psiv_out[1], idx, __ldg(A.cb[1] + hy), __ldg(A.ca[1] + hy),
-                               __ldg(A.ck[1] + hy), false, 0, nullptr, 0);
+                V4 g = dnb(m, p, C);
+                if (halo_psi_y) {
+                    const int r = yh_y - y0 + 4;
+                    const V4 psh = ldg_v4(psiv_in[1] + slab_index(G, 1, t, yh_y, yh_x));
+                    cpml4(g, psh, splat4(sCy[0][r]), splat4(sCy[1][r]), splat4(sCy[2][r]));
                 }
-                F4 vo = lds4<T>(S + L::OFF_VY, (hy - y0 + 4) * TX + 4 * c);
-                F4 vn;
+                V4 vn = fma4(ndtr, g, lds<T>(S + L::OFF_VY, (yh_y - y0 + 4) * TX + 4 * yh_c));
+                if (!full_tile || !yh_in) {
+                    F4 f = to_f4(vn);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        f.v[i] = (yh_in && yh_x + i < G.nx) ? f.v[i] : 0.f;
+                    vn = to_v4(f);
+                }
+                stsf(svy + (yh_y - y0 + 4) * TX + 4 * yh_c, vn);
+            } else if (do_xhalo) {
+                const int lrow = (xh_r + 8) * L::PW, lx = xh_x - x0 + 8;
+                V4 g = dx4(lds<T>(Sp, lrow + lx - 4), lds<T>(Sp, lrow + lx), lds<T>(Sp, lrow + lx + 4), C);
+                if (halo_psi_x) {
+                    const int cx = xh_x - x0 + 4;
+                    const V4 psh = ldg_v4(psiv_in[0] + slab_index(G, 0, t, xh_y, xh_x));
+                    cpml4(g, psh, ldsf(&sCx[0][cx]), ldsf(&sCx[1][cx]), ldsf(&sCx[2][cx]));
+                }
+                V4 vn = fma4(ndtr, g, lds<T>(S + L::OFF_VX, xh_r * L::VXW + lx));
+                F4 f = to_f4(vn);
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    vn.v[i] = (yin && hx + i < G.nx) ? vo.v[i] - A.dtr * g.v[i] : 0.f;
-                sts4f(svy + (hy - y0 + 4) * TX + 4 * c, vn);
+                    f.v[i] = (xh_y < G.ny && xh_x + i >= 0 && xh_x + i < G.nx) ? f.v[i] : 0.f;
+                stsf(svx + xh_r * L::SVXW + (xh_x - x0 + 4), to_v4(f));
             }
         }
 
-        // all v' of plane t are in shared memory; abort together on a timeout
+        // all v' of plane t are in shared memory; stop together on a timeout
         if (__syncthreads_or(ok ? 0 : 1)) {
             if (tid == 0) {
                 atomicOr(A.err, ERR_TIMEOUT);
@@ -395,49 +538,60 @@ __global__ void __launch_bounds__(NTHREADS, 2)
 
         if (active) {
             // ---- pressure step at plane t
-            F4 hx4 = dx4(lds4f(svx + ty * (TX + 8) + 4 * tx), lds4f(svx + ty * (TX + 8) + 4 * tx + 4),
-                         lds4f(svx + ty * (TX + 8) + 4 * tx + 8), cw);
-            F4 hy4;
+            const float *sxr = svx + ty * L::SVXW + 4 * tx;
+            V4 hx4 = dx4(ldsf(sxr), ldsf(sxr + 4), ldsf(sxr + 8), C);
+            V4 hy4;
             {
-                F4 m[4], p[4];
+                V4 m[4], p[4];
 #pragma unroll
                 for (int l = 1; l <= 4; ++l) {
-                    m[l - 1] = lds4f(svy + (ty + 4 - l) * TX + 4 * tx);
-                    p[l - 1] = lds4f(svy + (ty + 4 + l) * TX + 4 * tx);
+                    m[l - 1] = ldsf(svy + (ty + 4 - l) * TX + 4 * tx);
+                    p[l - 1] = ldsf(svy + (ty + 4 + l) * TX + 4 * tx);
                 }
-                hy4 = dn4(m, p, cw);
+                hy4 = dnb(m, p, C);
             }
-            F4 hz4;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                hz4.v[i] = cw[0] * (vzq[5].v[i] - vzq[3].v[i]) + cw[1] * (vzq[6].v[i] - vzq[2].v[i]) +
-                           cw[2] * (vzq[7].v[i] - vzq[1].v[i]) + cw[3] * (vzq[8].v[i] - vzq[0].v[i]);
-            if (gy < G.ny && (gx < G.lo[0] || gx + 3 >= G.nx - G.hi[0]))
-                cpml_x<T>(G, A, hx4, psip[0], psip[0], t, gy, gx, true, stape[0], 2);
-            if (row_ok && in_slab(gy, G.ny, G.lo[1], G.hi[1])) {
-                const long long idx = slab_index(G, 1, t, gy, gx);
-                cpml_yz<T>(hy4, psip[1], psip[1], idx, __ldg(A.cb[1] + gy), __ldg(A.ca[1] + gy),
-                           __ldg(A.ck[1] + gy), true, nvalid, stape[1], 2);
+            if (own_x) {
+                const int cx = 4 * tx + 4;
+                const long long ix = slab_index(G, 0, t, gy, gx);
+                const V4 pspx = ldg_v4(psip[0] + ix);
+                if (stape[0])
+                    tape4(stape[0], ix, 2, hx4, pspx);
+                const V4 pn = cpml4(hx4, pspx, ldsf(&sCx[0][cx]), ldsf(&sCx[1][cx]), ldsf(&sCx[2][cx]));
+                Io<T>::st4(psip[0] + ix, to_f4(pn));
             }
-            if (row_ok && in_slab(t, G.nz, G.lo[2], G.hi[2])) {
-                const long long idx = slab_index(G, 2, t, gy, gx);
-                cpml_yz<T>(hz4, psip[2], psip[2], idx, __ldg(A.cb[2] + t), __ldg(A.ca[2] + t),
-                           __ldg(A.ck[2] + t), true, nvalid, stape[2], 2);
+            if (own_y) {
+                const long long iy = slab_index(G, 1, t, gy, gx);
+                const V4 pspy = ldg_v4(psip[1] + iy);
+                if (stape[1])
+                    tape4(stape[1], iy, 2, hy4, pspy);
+                const V4 pn = cpml4(hy4, pspy, splat4(sCy[0][ty + 4]), splat4(sCy[1][ty + 4]), splat4(sCy[2][ty + 4]));
+                Io<T>::st4(psip[1] + iy, to_f4(pn));
             }
-            const F4 kd = lds4f(reinterpret_cast<const float *>(S + L::OFF_K) + ty * TX + 4 * tx);
-            F4 pn, sb;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                sb.v[i] = hx4.v[i] + hy4.v[i] + hz4.v[i];
-                pn.v[i] = own_ok[i] ? pq[0].v[i] - kd.v[i] * sb.v[i] : 0.f;
+            if (zs_p) {
+                const long long izp = slab_index(G, 2, t, gy, gx);
+                const V4 pspz = ldg_v4(psip[2] + izp);
+                if (stape[2])
+                    tape4(stape[2], izp, 2, hz4, pspz);
+                const V4 pn = cpml4(hz4, pspz, splat4(__ldg(A.cb[2] + t)), splat4(__ldg(A.ca[2] + t)),
+                                    splat4(__ldg(A.ck[2] + t)));
+                Io<T>::st4(psip[2] + izp, to_f4(pn));
             }
-            if (t == sz && gy == sy && sx >= gx && sx < gx + 4)
-                pn.v[sx - gx] += wsrc;
+            // nkdt holds -dt K / vscale (zero beyond the grid)
+            const V4 nkd = ldsf(reinterpret_cast<const float *>(S + L::OFF_K) + ty * TX + 4 * tx);
+            const V4 sb = add4(add4(hx4, hy4), hz4);
+            V4 pn = V4{fma2(nkd.a, sb.a, pt.a), fma2(nkd.b, sb.b, pt.b)};
+            if (src_here && t == sz) {
+                const int i = sx - gx;   // select, not a dynamic register index
+                pn.a.x += (i == 0) ? wsrc : 0.f;
+                pn.a.y += (i == 1) ? wsrc : 0.f;
+                pn.b.x += (i == 2) ? wsrc : 0.f;
+                pn.b.y += (i == 3) ? wsrc : 0.f;
+            }
             if (row_ok) {
-                const long long o = (long long)t * G.plane + (long long)gy * G.nxp + gx;
-                Io<T>::st4(p_out + o, pn);
+                const long long o = (long long)t * G.plane + rowofs;
+                Io<T>::st4(reinterpret_cast<T *>(A.p_out) + fofs + o, to_f4(pn));
                 if (A.s_tape)
-                    sts4f(A.s_tape + fofs + o, sb);
+                    stsf(A.s_tape + fofs + o, sb);
             }
             if (rec_on) {
                 while (rc < r1 && A.rec[rc].x < t)
@@ -447,8 +601,10 @@ __global__ void __launch_bounds__(NTHREADS, 2)
                     if (q.x != t)
                         break;
                     if (q.y == gy && q.z >= gx && q.z < gx + 4) {
-                        // re-read through the storage type so traces equal the stored state
-                        T tmp = T(pn.v[q.z - gx]);
+                        const int i = q.z - gx;
+                        const float v = i == 0 ? pn.a.x : (i == 1 ? pn.a.y : (i == 2 ? pn.b.x : pn.b.y));
+                        // read back through the storage type so traces equal the stored state
+                        T tmp = T(v);
                         A.traces[((long long)shot * A.nt_max + A.t) * A.nrec + q.w] = Io<T>::ld1(&tmp);
                     }
                 }
@@ -458,11 +614,6 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         if (tid == 0 && it + NSTAGE < niter) {
             fence_proxy_async_smem();
             issue(it + NSTAGE);
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            pq[k] = pq[k + 1];
-            vzq[k] = vzq[k + 1];
         }
     }
 }
@@ -497,41 +648,27 @@ cudaError_t launch_step(const fdtd_ctx *c, const StepArgs &a, int set)
     }
 }
 
-int step_smem_bytes(int storage)
+template <typename T>
+static int occupancy_t(int *blocks)
 {
-    switch (storage) {
-    case FDTD_F16:
-        return StageLayout<__half>::SMEM;
-    case FDTD_BF16:
-        return StageLayout<__nv_bfloat16>::SMEM;
-    default:
-        return StageLayout<float>::SMEM;
-    }
+    using L = StageLayout<T>;
+    cudaFuncSetAttribute(fdtd_step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fdtd_step_kernel<T>, NTHREADS, L::SMEM) ==
+                   cudaSuccess
+               ? 0
+               : -1;
 }
 
 int step_occupancy(int storage, int *blocks)
 {
-    cudaError_t e;
     switch (storage) {
     case FDTD_F16:
-        cudaFuncSetAttribute(fdtd_step_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             StageLayout<__half>::SMEM);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fdtd_step_kernel<__half>, NTHREADS,
-                                                          StageLayout<__half>::SMEM);
-        break;
+        return occupancy_t<__half>(blocks);
     case FDTD_BF16:
-        cudaFuncSetAttribute(fdtd_step_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             StageLayout<__nv_bfloat16>::SMEM);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fdtd_step_kernel<__nv_bfloat16>, NTHREADS,
-                                                          StageLayout<__nv_bfloat16>::SMEM);
-        break;
+        return occupancy_t<__nv_bfloat16>(blocks);
     default:
-        cudaFuncSetAttribute(fdtd_step_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             StageLayout<float>::SMEM);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fdtd_step_kernel<float>, NTHREADS,
-                                                          StageLayout<float>::SMEM);
+        return occupancy_t<float>(blocks);
     }
-    return e == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace fdtd

@@ -201,6 +201,10 @@ def preset(name: str) -> Workload:
         # R = 1e-8, 10 Hz Ricker 30 cells below the top face, 1000 steps.
         return Workload("layered512", (512, 512, 512), 10.0, 1000, 10.0, (20,) * 6, 1e-8,
                         model="layered", seed=2, src_depth=30)
+    if name == "layered256":
+        # smaller grid of the same recipe (profiling captures, quick runs)
+        return Workload("layered256", (256, 256, 256), 10.0, 1000, 10.0, (20,) * 6, 1e-8,
+                        model="layered", seed=2, src_depth=30)
     if name == "layered1024":
         return Workload("layered1024", (1024, 1024, 1024), 10.0, 500, 10.0, (20,) * 6, 1e-8,
                         model="layered", seed=3, src_depth=30)
