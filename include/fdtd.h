@@ -202,6 +202,29 @@ int fdtd_energy(fdtd_ctx *ctx, int shot, const int box[6], double *out);
  * [nshots][nt_max][nrec].  Synchronises. */
 int fdtd_misfit(fdtd_ctx *ctx, const float *dobs_dev, int nt, float *resid_dev, double *out);
 
+/* Largest n accepted by fdtd_misfit_noalloc: 4096 partial sums of 65536 values. */
+#define FDTD_NOALLOC_MISFIT_MAX 268435456LL
+
+/* The data misfit of fdtd_misfit, J = 1/2 sum_i (traces[i] - dobs[i])^2 over
+ * n floats accumulated in FP64, for callers that cannot allocate device
+ * memory.  The paper has no counterpart to this entry point.  It needs no
+ * context and allocates nothing, so it suits callers whose device memory
+ * belongs to another allocator with a fixed budget (e.g. a framework's caching
+ * allocator) or loops where cudaMalloc, which may synchronise the device, is
+ * not allowed.  Its scratch is a 33 KB static device array that every GPU
+ * loading the library keeps until the process exits.
+ *   traces_dev, dobs_dev: dev float [n]; resid_dev: dev float [n] receiving
+ *   traces - dobs, or NULL; out_host: host double receiving J; stream:
+ *   cudaStream_t (NULL = default).  Synchronises the stream.
+ *   EINVAL if a pointer is NULL or n is outside [1, FDTD_NOALLOC_MISFIT_MAX];
+ *   ECUDA if a CUDA call fails.
+ * The first call on a device looks up the scratch array's device address
+ * (set-up); make that first call before any stream capture.  All calls on a
+ * device share the scratch array, so calls that overlap on the GPU (e.g. on
+ * two streams at once) race and must be serialised by the caller. */
+int fdtd_misfit_noalloc(const float *traces_dev, const float *dobs_dev, long long n, float *resid_dev,
+                        double *out_host, void *stream);
+
 /* Chain rule of the learned CPML: from grad_cpml (layout of
  * fdtd_adjoint_step_n) and the per-cell ska_dev [L][3] given to
  * fdtd_set_cpml_ska, write gska_dev [L][3] = dJ/d(sigma, kappa, alpha). */

@@ -60,6 +60,8 @@ _SIGS = {
     "fdtd_sync": (c_int, [c_void_p]),
     "fdtd_energy": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
     "fdtd_misfit": (c_int, [c_void_p, c_void_p, c_int, c_void_p, ctypes.POINTER(c_double)]),
+    "fdtd_misfit_noalloc": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_void_p,
+                                    ctypes.POINTER(c_double), c_void_p]),
     "fdtd_cpml_ska_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "fdtd_mlp_forward": (c_int, [c_void_p, c_void_p, c_int, c_float, c_float, c_void_p, c_void_p, c_void_p]),
     "fdtd_mlp_backward": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_float, c_float,

@@ -225,6 +225,16 @@ cudaError_t launch_misfit(const fdtd_ctx *c, const float *dobs, int nt, float *r
     return cudaGetLastError();
 }
 
+// Misfit over a flat array of n values with `nblocks` partial sums written to
+// `part` and the result to `*out` (both device memory the caller provides).
+cudaError_t launch_misfit_flat(const float *tr, const float *dobs, float *resid, long long n, int nblocks,
+                               double *part, double *out, cudaStream_t s)
+{
+    misfit_kernel<<<nblocks, RED_THREADS, 0, s>>>(tr, dobs, resid, 1, n, n, 1, part);
+    finish_sum_kernel<<<1, RED_THREADS, 0, s>>>(part, nblocks, 0.5, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // learned CPML: per-cell (sigma, kappa, alpha) -> per-node (b, a, 1/kappa)
 // and the chain rule back (Sec. 3.2 coefficient formulas, in double)
