@@ -367,6 +367,8 @@ StepArgs base_args(const fdtd_ctx *c)
     for (int l = 0; l < 4; ++l)
         a.c[l] = (float)(kWeights[l] / c->d.h);
     a.dtr = (float)(c->d.dt * c->vscale);   // rho = 1
+    a.sscale = c->sscale;
+    a.inv_sscale = 1.f / c->sscale;
     a.src = c->nt_w > 0 ? c->src : nullptr;
     a.wavelet = c->wavelet;
     a.nt_w = c->nt_w;
@@ -542,6 +544,10 @@ int fdtd_create(const fdtd_desc *desc, void *workspace, size_t workspace_bytes, 
     c->tiles_x = L.tiles_x;
     c->tiles_y = L.tiles_y;
     c->vscale = 1.f;
+    // FP16 keeps the whole state scaled by 2^10 (exact): small late-time
+    // fields stay out of the FP16 subnormal range; the update is linear, so
+    // only source, receivers, field exchange and the energy see the scale
+    c->sscale = desc->storage == FDTD_F16 ? 1024.f : 1.f;
     c->ws = (unsigned char *)workspace;
     c->ws_bytes = workspace_bytes;
     unsigned char *w = c->ws;
@@ -903,6 +909,8 @@ int fdtd_get_field(fdtd_ctx *c, int which, int shot, float *dst)
             kind = d + 1;
         }
     }
+    if (!f32)
+        scale /= c->sscale;
     if (kind > 0 && c->g.slab[kind - 1] == 0) {
         CUDA_TRY(c, cudaMemsetAsync(dst, 0, (size_t)c->g.nz * c->g.ny * c->g.nx * 4, c->stream));
         return FDTD_OK;
@@ -957,6 +965,8 @@ int fdtd_set_field(fdtd_ctx *c, int which, int shot, const float *src)
             kind = d + 1;
         }
     }
+    if (!f32)
+        scale *= c->sscale;
     if (kind > 0 && c->g.slab[kind - 1] == 0)
         return FDTD_OK;
     CUDA_TRY(c, launch_field(c, false, ptr, const_cast<float *>(src), kind, scale, f32));
@@ -1005,6 +1015,7 @@ int fdtd_energy(fdtd_ctx *c, int shot, const int box[6], double *out)
     CUDA_TRY(c, launch_energy(c, p, box));
     CUDA_TRY(c, cudaMemcpyAsync(out, c->red + 608, 8, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    *out /= (double)c->sscale * (double)c->sscale;
     if (!std::isfinite(*out))
         return fail(c, FDTD_EDIVERGED, "non-finite energy");
     return FDTD_OK;

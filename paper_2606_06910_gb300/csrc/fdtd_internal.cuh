@@ -282,6 +282,7 @@ struct StepArgs {
     const float *cb[3], *ca[3], *ck[3];   // b, a, 1/kappa per node of each axis
     float c[4];                     // a_l / h
     float dtr;                      // dt * vscale / rho (velocity update)
+    float sscale, inv_sscale;       // stored state = sscale * physical state
     const int *src;                 // [nshots][3] (z, y, x)
     const float *wavelet;           // [nshots][nt_w]
     int nt_w;
@@ -304,6 +305,7 @@ struct fdtd_ctx {
     int es;                 // bytes per stored element
     int tiles_x, tiles_y, zchunk, nzchunks;
     float vscale;           // stored velocity = vscale * v (impedance scaling for 16-bit)
+    float sscale;           // every stored field is multiplied by sscale (2^10 for FP16, else 1)
     float c_max, c_min;
     int t;                  // time index
     int cur;                // ping-pong buffer holding the current state

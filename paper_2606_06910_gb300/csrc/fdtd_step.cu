@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
     // source of this shot
     const int sz = A.src ? A.src[3 * shot] : -1, sy = A.src ? A.src[3 * shot + 1] : -1,
               sx = A.src ? A.src[3 * shot + 2] : -1;
-    const float wsrc = (A.src && A.t < A.nt_w) ? A.wavelet[(long long)shot * A.nt_w + A.t] : 0.f;
+    const float wsrc = (A.src && A.t < A.nt_w) ? A.sscale * A.wavelet[(long long)shot * A.nt_w + A.t] : 0.f;
     const bool src_here = A.src && sy == gy && sx >= gx && sx < gx + 4 && sz >= z0 && sz < z1;
     // receivers of this tile (sorted by z)
     int rc = 0, r1 = 0;
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
                         const float v = i == 0 ? pn.a.x : (i == 1 ? pn.a.y : (i == 2 ? pn.b.x : pn.b.y));
                         // read back through the storage type so traces equal the stored state
                         T tmp = T(v);
-                        A.traces[((long long)shot * A.nt_max + A.t) * A.nrec + q.w] = Io<T>::ld1(&tmp);
+                        A.traces[((long long)shot * A.nt_max + A.t) * A.nrec + q.w] = A.inv_sscale * Io<T>::ld1(&tmp);
                     }
                 }
             }

@@ -49,9 +49,11 @@ class Fdtd:
     def __init__(self, shape, h, dt, *, nshots=1, cpml_cells=0, storage="f32", nt_max=1,
                  nrec_max=0, checkpoint_every=0, cpml_grad=False, device=None, stream=None):
         self.lib = _lib.load()
-        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = torch.device(device) if device is not None else torch.device("cuda")
         if self.device.type != "cuda":
             raise ValueError("Fdtd runs on a CUDA device only")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.shape = tuple(int(s) for s in shape)
         nz, ny, nx = self.shape
         self.nshots = int(nshots)
