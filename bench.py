@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--cells", type=int, default=None, help="override CPML cells per face (0: no CPML)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--forms", default="f16,bf16,adjoint,learned",
+                    help="comma list of forms measured after the main line ('' for none)")
     return ap.parse_args()
 
 
@@ -270,6 +272,143 @@ def run_ours(args, rank, world, local):
 
 
 # ----------------------------------------------------------------------------
+# the forms measured next to the FP32 path
+# ----------------------------------------------------------------------------
+def _timed(stream, fn):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def form_storage(storage, dev, nsteps=60, warm=10):
+    """16-bit storage on the 1024^3 layered workload (20 CPML cells)."""
+    import torch
+    from paper_2606_06910_gb300 import synth
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    w = synth.preset("layered1024")
+    sim = Fdtd(w.shape, w.h, w.dt, cpml_cells=w.cpml_cells, storage=storage, nt_max=w.nt, device=dev)
+    sim.set_model(torch.from_numpy(w.velocity()).to(dev))
+    sim.set_cpml(R=w.R, c_ref=w.vmax)
+    sim.inject(w.sources(), torch.from_numpy(w.wavelet()).to(dev))
+    sim.step(warm)
+    sim.sync()
+    secs = _timed(sim.stream, lambda: sim.step(nsteps))
+    sim.sync()
+    npts = float(np.prod(w.shape))
+    bytes_launch = algorithmic_bytes(w.shape, w.cpml_cells, 2)
+    peak, kind = measured_peaks()
+    del sim
+    torch.cuda.empty_cache()
+    ach = bytes_launch * nsteps / secs / 1e9
+    return {"workload": f"layered1024 {storage} storage, {nsteps} timed steps", "value": round(npts * nsteps / secs / 1e6, 1),
+            "unit": UNIT, "roofline_frac": round(ach / peak, 4), "achieved_GBps": round(ach, 1),
+            "accuracy": "vs FP64 oracle on the 128^3 instance: see tests/test_gpu_forms.py"}
+
+
+def form_adjoint(dev, nt=800):
+    """Forward with checkpoints + discrete adjoint, 256^3 x 16 shots, 128x128
+    receivers, checkpoint every 50 steps (gradient of the L2 misfit)."""
+    import torch
+    from paper_2606_06910_gb300 import synth
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    w = synth.preset("adjoint256")
+    rec = synth.receiver_grid(w.shape, w.cpml_cells, *w.extra["receivers"], z=w.cpml_cells[4])
+    c0 = synth.gaussian_smooth(w.velocity(), w.extra["smooth_sigma"])
+    sim = Fdtd(w.shape, w.h, w.dt, nshots=w.nshots, cpml_cells=w.cpml_cells, nt_max=nt, nrec_max=len(rec),
+               checkpoint_every=w.extra["checkpoint_every"], device=dev)
+    sim.set_model(torch.from_numpy(c0).to(dev))
+    sim.set_cpml(R=w.R, c_ref=w.vmax)
+    sim.inject(w.sources(), torch.from_numpy(w.wavelet(nt)).to(dev))
+    sim.record(rec)
+    dobs = torch.zeros_like(sim.traces)
+    grad = torch.zeros(w.shape, device=dev)
+    resid = torch.empty_like(sim.traces)
+    t_fwd = _timed(sim.stream, lambda: sim.step(nt))
+    J = sim.misfit(dobs, nt=nt, resid=resid)
+    t_adj = _timed(sim.stream, lambda: sim.adjoint(nt, resid, grad))
+    sim.sync()
+    ok = bool(torch.isfinite(grad).all()) and float(grad.abs().max()) > 0
+    pts = float(np.prod(w.shape)) * w.nshots * nt
+    del sim
+    torch.cuda.empty_cache()
+    return {"workload": f"adjoint256: 256^3 x {w.nshots} shots x {nt} steps, C=50", "value": round(pts / (t_fwd + t_adj) / 1e6, 1),
+            "unit": UNIT + " (forward + adjoint)", "forward_s": round(t_fwd, 3), "adjoint_s": round(t_adj, 3),
+            "misfit": J, "gradient_finite_nonzero": ok}
+
+
+def form_learned(dev, iters=30):
+    """Learned 6-cell CPML: trained through the adjoint on 96^3 homogeneous
+    reflection runs, evaluated on the 512^3 layered model (seed 5, 1000 steps)
+    against the polynomial grading with 6 and 20 cells: reflection ratio
+    ||traces - reference|| / ||reference|| at receivers just inside the layer,
+    the reference being the same interior inside a grid 64 nodes larger per
+    side."""
+    import torch
+    from paper_2606_06910_gb300 import synth
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    from paper_2606_06910_gb300.learned import reflection_task, train_learned_cpml
+    t0 = time.perf_counter()
+    task = reflection_task(n=96, L=6, nshots=8, seed=3, nt=220, f0=15.0, device=dev)
+    res = train_learned_cpml(task, iters=iters, lr=5e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    # evaluation on the 512^3 layered model
+    n, nt, h, margin = 512, 1000, 10.0, 64
+    vel = synth.layered_model((n,) * 3, seed=5)
+    dt = 0.5 * h / 4500.0
+    wav = synth.ricker(nt, dt, 10.0).astype(np.float32)[None, :]
+    src = np.array([[n // 2, n // 2 + 37, n // 2 - 51]], np.int32)
+    def face_rec(L):
+        k = 8
+        span = np.round(np.linspace(L + 2 + 20, n - 1 - L - 2 - 20, k)).astype(np.int32)
+        a, b = np.meshgrid(span, span, indexing="ij")
+        out = []
+        for plane in (26, n - 1 - 26):
+            out += [np.stack([np.full(a.size, plane), a.ravel(), b.ravel()], 1),
+                    np.stack([a.ravel(), np.full(a.size, plane), b.ravel()], 1),
+                    np.stack([a.ravel(), b.ravel(), np.full(a.size, plane)], 1)]
+        return np.concatenate(out).astype(np.int32)
+    rec = face_rec(20)
+    nb = n + 2 * margin
+    vb = np.pad(vel, margin, mode="edge")
+    big = Fdtd((nb,) * 3, h, dt, cpml_cells=20, nt_max=nt, nrec_max=len(rec), device=dev)
+    big.set_model(torch.from_numpy(vb).to(dev))
+    big.set_cpml(R=1e-8, c_ref=4500.0)
+    big.inject(src + margin, torch.from_numpy(wav).to(dev))
+    big.record(rec + margin)
+    big.step(nt)
+    ref = big.traces.clone()
+    big.close()
+    del big
+    torch.cuda.empty_cache()
+    out = {}
+    for name, cells in (("learned_6", 6), ("polynomial_6", 6), ("polynomial_20", 20)):
+        sim = Fdtd((n,) * 3, h, dt, cpml_cells=cells, nt_max=nt, nrec_max=len(rec), device=dev)
+        sim.set_model(torch.from_numpy(vel).to(dev))
+        if name == "learned_6":
+            res["model"].set_frequency(10.0)
+            ska, _ = res["model"].ska()
+            sim.set_cpml_ska(ska)
+        else:
+            sim.set_cpml(R=1e-8, kappa_max=5.0, alpha_frac=0.05, q=3, c_ref=4500.0)
+        sim.inject(src, torch.from_numpy(wav).to(dev))
+        sim.record(rec)
+        secs = _timed(sim.stream, lambda: sim.step(nt))
+        r = float(((sim.traces - ref) ** 2).sum() / (ref ** 2).sum()) ** 0.5
+        out[name] = {"reflection": round(r, 5), "Mpoints_s": round(n ** 3 * nt / secs / 1e6, 1)}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    return {"workload": "train 96^3 homogeneous (8 shots, 220 steps, "
+                        f"{iters} Adam steps); evaluate 512^3 layered seed 5, 1000 steps",
+            "train_s": round(t_train, 1), "train_reflection_polynomial_6": round(res["poly_eval"], 5),
+            "train_reflection_learned_6": round(res["learned_eval"], 5), "eval": out}
+
+
+# ----------------------------------------------------------------------------
 # the FP64 oracle (CPU baseline and reference arm)
 # ----------------------------------------------------------------------------
 def oracle_sample(preset: str, nsteps: int, warm: int = 0):
@@ -331,6 +470,22 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     out = run_ours(args, rank, world, local)
+    if rank == 0 and world == 1 and args.forms:
+        import torch
+        dev = torch.device("cuda", local)
+        forms = {}
+        for f in [x for x in args.forms.split(",") if x]:
+            torch.cuda.empty_cache()
+            try:
+                if f in ("f16", "bf16"):
+                    forms[f] = form_storage(f, dev)
+                elif f == "adjoint":
+                    forms[f] = form_adjoint(dev)
+                elif f == "learned":
+                    forms[f] = form_learned(dev)
+            except Exception as e:  # report, keep the main line
+                forms[f] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        out["forms"] = forms
     if rank == 0:
         if not args.no_cpu_baseline:
             import oracle
