@@ -123,11 +123,11 @@ def step_kernel_traffic(storage: str, shape):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     scaled to this grid, or None when the kernel source changed since."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_2606_06910_gb300", "csrc", "fdtd_step.cu")
+    srcs = [os.path.join(ROOT, "paper_2606_06910_gb300", "csrc", f) for f in ("fdtd_step.cu", "fdtd_internal.cuh")]
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256(b"".join(open(s, "rb").read() for s in srcs)).hexdigest()[:16]
     e = d.get(storage)
     if not e or e.get("kernel_sha") != h:
         return None

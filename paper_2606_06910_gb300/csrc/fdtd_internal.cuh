@@ -194,10 +194,15 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-// bring the line holding p into L2 (no register result, no wait)
+// bring the line holding p into L2 (or L1 with FDTD_PREFETCH == 2); no
+// register result, no wait
 __device__ __forceinline__ void prefetch_l2(const void *p)
 {
+#if defined(FDTD_PREFETCH) && FDTD_PREFETCH == 2
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+#else
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+#endif
 }
 
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
