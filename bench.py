@@ -254,11 +254,7 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": f"{args.preset}: {shape[0]}^3 layered 1500-4500 m/s, CPML {cells[0]} cells, "
-                               f"R=1e-8, 10 Hz Ricker, {nt} time steps per bench step",
-                   "grid": list(shape), "time_steps_per_step": nt, "cpml_cells": list(cells),
-                   "storage": args.storage, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (state >= 4 GB per replica)"},
+        "config": workload_config(args, shape, cells, nt, world),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None if traffic is None else round(traffic),
                      "peak_source": f"{peak_kind} hbm_gbs", "kernel": "fdtd_step_kernel",
@@ -431,25 +427,46 @@ def oracle_sample(preset: str, nsteps: int, warm: int = 0):
     return float(np.prod(w.shape)) * nsteps / dt / 1e6, dt, threads
 
 
+def workload_config(args, shape, cells, nt, world):
+    return {"workload": f"{args.preset}: {shape[0]}^3 layered 1500-4500 m/s, CPML {cells[0]} cells, "
+                        f"R=1e-8, 10 Hz Ricker, {nt} time steps per bench step",
+            "grid": list(shape), "time_steps_per_step": nt, "cpml_cells": list(cells),
+            "storage": args.storage, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (state >= 4 GB per replica)"}
+
+
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, on the same
+    workload; each bench step is a bounded sample of it (one time step of the
+    full grid)."""
     if rank != 0:
         return None
     import oracle
+    from oracle import oracle as O
+    from paper_2606_06910_gb300 import synth
     oracle.build()
-    per, times = [], []
+    w = synth.preset(args.preset)
+    cells = w.cpml_cells if args.cells is None else (args.cells,) * 6
+    nt = args.nt or w.nt
+    vel = w.velocity().astype(np.float64)
+    g = O.Grid(vel * vel, w.h, w.dt, O.make_profiles(w.shape, cells, w.h, w.dt, w.c_max, R=w.R))
+    st = O.State(w.shape)
+    src = tuple(w.sources()[0])
+    wav = synth.ricker(args.warmup + args.steps + 1, w.dt, w.f0)
+    times = []
     for k in range(args.warmup + args.steps):
-        mpts, secs, threads = oracle_sample(args.preset, 1)
+        t = time.perf_counter()
+        O.run(g, st, 1, k, src, wav)
         if k >= args.warmup:
-            per.append(mpts)
-            times.append(secs)
-    value = float(np.prod(__import__("paper_2606_06910_gb300.synth", fromlist=["x"]).preset(args.preset).shape)) \
-        * len(times) / sum(times) / 1e6
-    sample = f"{args.preset} full grid, 1 oracle time step per bench step (FP64, OpenMP)"
+            times.append(time.perf_counter() - t)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = float(np.prod(w.shape)) * len(times) / sum(times) / 1e6
+    sample = f"{args.preset} full grid, one FP64 oracle time step per bench step (OpenMP, {threads} threads)"
     return {
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.preset} (one time step per bench step)"},
+        "config": workload_config(args, w.shape, cells, nt, world),
         "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
