@@ -32,6 +32,7 @@ cudaError_t launch_adam(float *th, const float *g, float *m, float *v, int n, fl
 cudaError_t launch_adj_inject(const fdtd_ctx *c, const float *resid, int n);
 cudaError_t launch_grad_vel(const fdtd_ctx *c, float *grad_vel);
 cudaError_t adjoint_step(fdtd_ctx *c, const float *s_tape, float *const slab_tape[3], bool want_prof);
+cudaError_t adjoint_step_tiled(fdtd_ctx *c, const float *s_tape);
 int mlp_nparam();
 int mlp_bwd_max();
 }  // namespace fdtd
@@ -237,7 +238,18 @@ int build_maps(fdtd_ctx *c)
             return st;
     }
     const uint32_t bK[4] = {TX, TY, 1, 1};
-    return make_map(c, &c->mapK, c->kdt, 3, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bK);
+    int st = make_map(c, &c->mapK, c->kdt, 3, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bK);
+    if (st || c->ncp == 0)
+        return st;
+    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const uint32_t b40[4] = {TX + 8, TY + 8, 1, 1}, bx[4] = {TX + 8, TY, 1, 1}, by[4] = {TX, TY + 8, 1, 1};
+    if ((st = make_map(c, &c->amaps[0], c->ap, 4, f32, 4, b40)) || (st = make_map(c, &c->amaps[1], c->ap, 4, f32, 4, bQ)) ||
+        (st = make_map(c, &c->amaps[2], c->kdt, 3, f32, 4, b40)) ||
+        (st = make_map(c, &c->amaps[3], c->av[0], 4, f32, 4, bx)) ||
+        (st = make_map(c, &c->amaps[4], c->av[1], 4, f32, 4, by)) ||
+        (st = make_map(c, &c->amaps[5], c->av[2], 4, f32, 4, bQ)))
+        return st;
+    return FDTD_OK;
 }
 
 // Choose the z-chunk so that the grid fills the resident CTA slots evenly,
@@ -843,7 +855,12 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
             for (int d = 0; d < 3; ++d)
                 slab[d] = c->tape_slab[d] ? c->tape_slab[d] + (size_t)(k - s0) * c->d.nshots * c->g.slab[d] * 4
                                           : nullptr;
-            CUDA_TRY(c, adjoint_step(c, c->tape_s + (size_t)(k - s0) * c->d.nshots * c->g.vol, slab, want_prof));
+            const float *sk = c->tape_s + (size_t)(k - s0) * c->d.nshots * c->g.vol;
+            // the tiled kernels carry no profile gradient; that path keeps the node-per-thread kernels
+            if (want_prof)
+                CUDA_TRY(c, adjoint_step(c, sk, slab, true));
+            else
+                CUDA_TRY(c, adjoint_step_tiled(c, sk));
         }
     }
     if (grad_vel)

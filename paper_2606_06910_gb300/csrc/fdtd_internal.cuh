@@ -345,5 +345,8 @@ struct fdtd_ctx {
     float *gprof;           // [3][3][nmax]
     CUtensorMap maps[2][5]; // per ping-pong set: P halo, P queue, VX, VY, VZ
     CUtensorMap mapK;
+    // adjoint (FP32, built when checkpoint slots exist): lam_p 40x40 and
+    // 32x32, kdt 40x40, lam_v_x 40x32, lam_v_y 32x40, lam_v_z 32x32
+    CUtensorMap amaps[6];
     char last_error[256];
 };

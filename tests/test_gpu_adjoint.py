@@ -187,3 +187,55 @@ def test_autograd_function_matches_direct_adjoint():
     J, g, _ = _gpu_gradient(case)
     assert abs(float(loss) - J) <= 1e-5 * J
     assert np.allclose(vel.grad.cpu().numpy(), g, rtol=1e-5, atol=1e-6 * np.max(np.abs(g)))
+
+
+@pytest.mark.parametrize("zchunk", [None, 8])
+def test_adjoint_state_matches_oracle_multi_tile(monkeypatch, zchunk):
+    """Adjoint state and dJ/dc after 5 steps against the oracle's transpose,
+    field by field, on a grid of 3 x 3 tiles with ragged x and y tails, six
+    unequal layers and two shots; with the z range split into chunks of 8
+    (ragged last chunk) and with the default chunking."""
+    if zchunk is not None:
+        monkeypatch.setenv("FDTD_ZCHUNK", str(zchunk))
+    Fdtd = _Fdtd()
+    shape, cells, h, c = (37, 70, 75), (5, 6, 4, 7, 3, 5), 10.0, 2500.0
+    dt = 0.5 * h / c
+    n, C, nshots = 5, 3, 2
+    rng = np.random.default_rng(21)
+    vel = rng.uniform(1500, c, size=shape).astype(np.float32)
+    sim = Fdtd(shape, h, dt, nshots=nshots, cpml_cells=cells, nt_max=n, checkpoint_every=C)
+    sim.set_model(torch.from_numpy(vel).cuda())
+    sim.set_cpml(R=1e-4, c_ref=c)
+    g = O.Grid(vel.astype(np.float64) ** 2, h, dt, O.make_profiles(shape, cells, h, dt, c, R=1e-4))
+    refs = []
+    for s in range(nshots):
+        x = _rand_state(shape, cells, 30 + s, h, dt)
+        y = synth.random_state(shape, cells, seed=40 + s)
+        for k in FIELDS:
+            sim.set(k, torch.from_numpy(x[k]).cuda(), s)
+            sim.set("adj_" + k, torch.from_numpy(y[k]).cuda(), s)
+        fwd = O.State(shape)
+        for k in FIELDS:
+            fwd[k] = x[k].astype(np.float64)
+        starts = []
+        for _ in range(n):
+            starts.append(fwd.copy())
+            O.run(g, fwd, 1)
+        adj = O.State(shape)
+        for k in FIELDS:
+            adj[k] = y[k].astype(np.float64)
+        gK = np.zeros(shape)
+        for k in range(n - 1, -1, -1):
+            O.adjoint_step(g, starts[k], adj, gK)
+        refs.append((adj, gK))
+    sim.step(n)
+    grad = torch.zeros(shape, device="cuda")
+    sim.adjoint(n, None, grad)
+    sim.sync()
+    for s in range(nshots):
+        for k in FIELDS:
+            e2, em = rel_errors(sim.get("adj_" + k, s).cpu().numpy(), refs[s][0][k])
+            assert e2 <= 1e-4 and em <= 1e-3, (s, k, e2, em)
+    gref = (refs[0][1] + refs[1][1]) * 2.0 * vel.astype(np.float64)
+    e2, em = rel_errors(grad.cpu().numpy(), gref)
+    assert e2 <= 1e-4 and em <= 1e-3, (e2, em)
