@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--cells", type=int, default=None, help="override CPML cells per face (0: no CPML)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--forms", default="f16,bf16,adjoint,learned",
+    ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock",
                     help="comma list of forms measured after the main line ('' for none)")
     return ap.parse_args()
 
@@ -305,6 +305,37 @@ def form_storage(storage, dev, nsteps=60, warm=10):
             "accuracy": "vs FP64 oracle on the 128^3 instance: see tests/test_gpu_forms.py"}
 
 
+def form_tblock(dev, nsteps=96, warm=8):
+    """Temporal blocking sweep k = 1, 2, 4 on the 512^3 layered workload
+    (20 CPML cells): Mpoints/s of each k, and whether the final state of k = 2
+    and 4 equals the one of k = 1 node for node."""
+    import torch
+    from paper_2606_06910_gb300 import synth
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    w = synth.preset("layered512")
+    npts = float(np.prod(w.shape))
+    out, p_ref = {}, None
+    for k in (1, 2, 4):
+        sim = Fdtd(w.shape, w.h, w.dt, cpml_cells=w.cpml_cells, nt_max=w.nt, tblock_k=k, device=dev)
+        sim.set_model(torch.from_numpy(w.velocity()).to(dev))
+        sim.set_cpml(R=w.R, c_ref=w.vmax)
+        sim.inject(w.sources(), torch.from_numpy(w.wavelet()).to(dev))
+        sim.step(warm)
+        sim.sync()
+        secs = _timed(sim.stream, lambda: sim.step(nsteps))
+        sim.sync()
+        p = sim.get("p")
+        entry = {"value": round(npts * nsteps / secs / 1e6, 1), "ms_per_step": round(secs / nsteps * 1e3, 4)}
+        if p_ref is None:
+            p_ref = p.clone()
+        else:
+            entry["identical_to_k1"] = bool(torch.equal(p, p_ref))
+        out[f"k{k}"] = entry
+        del sim, p
+        torch.cuda.empty_cache()
+    return {"workload": f"layered512, {warm} + {nsteps} timed steps, z bands of 48 planes", "unit": UNIT, **out}
+
+
 def form_adjoint(dev, nt=800):
     """Forward with checkpoints + discrete adjoint, 256^3 x 16 shots, 128x128
     receivers, checkpoint every 50 steps (gradient of the L2 misfit)."""
@@ -500,6 +531,8 @@ def main():
                     forms[f] = form_adjoint(dev)
                 elif f == "learned":
                     forms[f] = form_learned(dev)
+                elif f == "tblock":
+                    forms[f] = form_tblock(dev)
             except Exception as e:  # report, keep the main line
                 forms[f] = {"error": f"{type(e).__name__}: {e}"[:300]}
         out["forms"] = forms

@@ -83,7 +83,7 @@ typedef struct {
     double dt;               /* time step [s] */
     int cpml_cells[6];       /* CPML cells per face (-x,+x,-y,+y,-z,+z), 0 = none */
     int storage;             /* fdtd_storage */
-    int tblock_k;            /* time steps per pass over HBM: 1 (default) */
+    int tblock_k;            /* time steps per block: 1, 2 or 4 (see fdtd_step_n) */
     int nt_max;              /* capacity of wavelet and trace buffers (steps) */
     int nrec_max;            /* receiver capacity */
     int checkpoint_every;    /* > 0: keep checkpoints every C steps (adjoint) */
@@ -99,7 +99,7 @@ const char *fdtd_status_string(int status);
 
 /* Bytes of device workspace that fdtd_create needs for `desc` (host-only
  * computation; no CUDA call).  EINVAL if desc is invalid: a dimension < 1,
- * h or dt <= 0, 2 * cells > n on an axis, storage unknown, tblock_k not 1,
+ * h or dt <= 0, 2 * cells > n on an axis, storage unknown, tblock_k not 1, 2 or 4,
  * nt_max < 1, nshots outside [1, 1024], nrec_max < 0, checkpoint_every < 0,
  * or cpml_grad set without checkpoint_every. */
 int fdtd_workspace_bytes(const fdtd_desc *desc, size_t *bytes);
@@ -158,7 +158,18 @@ int fdtd_record(fdtd_ctx *ctx, const int *rec_zyx, int nrec, float *traces_dev);
 /* Advance every shot by n full time steps (one fused kernel per step).
  * With checkpoint_every = C > 0 the state is saved before every step whose
  * index is a multiple of C (up to nt_max).  ESTATE before set_model /
- * set_cpml; EINVAL if n < 0. */
+ * set_cpml; EINVAL if n < 0.
+ *
+ * Temporal blocking, tblock_k = k in {2, 4} (the enlarged-ghost idea of
+ * paper Sec. 3.3, g = 2 r s, applied to z bands of one device): whole
+ * blocks of k steps cut the z range into bands of >= 8 planes (48 by
+ * default, environment variable FDTD_TBAND); step s of a block runs on a
+ * band as soon as step s - 1 has finished that band and its two neighbours,
+ * so a band's intermediate states are read back while they can still be held
+ * in L2.  The library then enqueues on k internal streams that join `stream`
+ * before the call returns (events; no host wait).  Results are identical to
+ * k = 1, node for node.  Steps left over after the whole blocks, and any
+ * block with a checkpoint inside it, run as single steps. */
 int fdtd_step_n(fdtd_ctx *ctx, int n);
 
 /* Discrete adjoint of the last n = current-time steps (run backwards from the

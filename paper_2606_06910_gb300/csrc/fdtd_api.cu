@@ -14,7 +14,7 @@
 #include "fdtd_internal.cuh"
 
 namespace fdtd {
-cudaError_t launch_step(const fdtd_ctx *c, const StepArgs &a, int set);
+cudaError_t launch_step(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream);
 int step_occupancy(int storage, int *blocks);
 cudaError_t launch_model(fdtd_ctx *c, const float *vel);
 cudaError_t launch_field(const fdtd_ctx *c, bool get, void *internal, float *dense, int kind, float scale,
@@ -94,8 +94,8 @@ const char *check_desc(const fdtd_desc *d)
     }
     if (d->storage != FDTD_F32 && d->storage != FDTD_F16 && d->storage != FDTD_BF16)
         return "unknown storage";
-    if (d->tblock_k != 1)
-        return "tblock_k must be 1";
+    if (d->tblock_k != 1 && d->tblock_k != 2 && d->tblock_k != 4)
+        return "tblock_k must be 1, 2 or 4";
     if (d->nt_max < 1)
         return "nt_max must be >= 1";
     if (d->nshots < 1 || d->nshots > 1024)
@@ -281,6 +281,15 @@ void choose_zchunk(fdtd_ctx *c)
             best = zc;
         }
     }
+    // Large grids: chunks of about 48 planes (FP32) or 96 (16-bit storage).
+    // CTAs that start together on short chunks stay close in z, so the halo
+    // planes that neighbouring tiles read are still in L2; measured on
+    // 256^3 x 16 shots, 512^3 and 1024^3 this beats the wave count above.
+    const int target = c->d.storage == FDTD_F32 ? 48 : 96;
+    const int kt = (nz + target - 1) / target;
+    if (per_z * kt >= 2 * slots) {
+        best = (nz + kt - 1) / kt;
+    }
     if (const char *e = getenv("FDTD_ZCHUNK")) {
         const int v = atoi(e);
         if (v > 0)
@@ -362,6 +371,53 @@ bool fault_is(const char *what)
     return f && strcmp(f, what) == 0;
 }
 
+// Streams and events of temporal blocking (tblock_k > 1).  The band height
+// is 48 planes unless FDTD_TBAND says otherwise; it is never below 8, the
+// dependence radius of one step along z.
+int make_tblock(fdtd_ctx *c)
+{
+    const int k = c->d.tblock_k;
+    if (k <= 1)
+        return FDTD_OK;
+    int band = 48;
+    if (const char *e = getenv("FDTD_TBAND")) {
+        const int v = atoi(e);
+        if (v > 0)
+            band = v;
+    }
+    c->tb_band = std::max(8, band);
+    c->tb_nb = std::max(1, c->g.nz / c->tb_band);
+    const size_t nev = (size_t)k * c->tb_nb;
+    c->tb_ev = new (std::nothrow) cudaEvent_t[nev]();
+    if (!c->tb_ev)
+        return FDTD_ENOMEM;
+    for (int s = 0; s < k; ++s)
+        if (cudaStreamCreateWithFlags(&c->tb_stream[s], cudaStreamNonBlocking) != cudaSuccess)
+            return FDTD_ECUDA;
+    if (cudaEventCreateWithFlags(&c->tb_entry, cudaEventDisableTiming) != cudaSuccess)
+        return FDTD_ECUDA;
+    for (size_t i = 0; i < nev; ++i)
+        if (cudaEventCreateWithFlags(&c->tb_ev[i], cudaEventDisableTiming) != cudaSuccess)
+            return FDTD_ECUDA;
+    return FDTD_OK;
+}
+
+void free_ctx(fdtd_ctx *c)
+{
+    if (c->tb_ev) {
+        for (size_t i = 0; i < (size_t)c->d.tblock_k * c->tb_nb; ++i)
+            if (c->tb_ev[i])
+                cudaEventDestroy(c->tb_ev[i]);
+        delete[] c->tb_ev;
+    }
+    if (c->tb_entry)
+        cudaEventDestroy(c->tb_entry);
+    for (int s = 0; s < 4; ++s)
+        if (c->tb_stream[s])
+            cudaStreamDestroy(c->tb_stream[s]);
+    delete c;
+}
+
 StepArgs base_args(const fdtd_ctx *c)
 {
     StepArgs a;
@@ -369,6 +425,8 @@ StepArgs base_args(const fdtd_ctx *c)
     a.g = c->g;
     a.tiles_x = c->tiles_x;
     a.zchunk = c->zchunk;
+    a.zbase = 0;
+    a.zend = c->g.nz;
     const int nmax = nmax_of(c->g);
     for (int d = 0; d < 3; ++d) {
         a.cb[d] = c->coef + (d * 3 + 0) * nmax;
@@ -393,6 +451,65 @@ StepArgs base_args(const fdtd_ctx *c)
     return a;
 }
 
+bool needs_ckpt(const fdtd_ctx *c, int t)
+{
+    const int C = c->d.checkpoint_every;
+    return C > 0 && t % C == 0 && t / C < c->ncp;
+}
+
+// m blocks of k = tblock_k steps.  The z range is cut into bands of at least
+// 8 planes (the reach of one step along z).  Step s of a block runs on band b
+// as soon as step s - 1 has finished bands b - 1, b and b + 1: each step has
+// its own stream and waits on the event of band b + 1 of the step before
+// (the previous block's last step, for s = 0).  Writes of step s land in the
+// ping-pong set that step s - 2 wrote, whose readers (step s - 1 on bands
+// b - 1 .. b + 1) are then done, so two sets suffice.  A band's intermediate
+// state is read again soon after it is written, while it can still be held
+// in L2.  Every node is computed exactly as by single steps.
+int launch_blocks(fdtd_ctx *c, int m)
+{
+    const int k = c->d.tblock_k, nb = c->tb_nb;
+    auto ev = [&](int s, int b) { return c->tb_ev[(size_t)s * nb + b]; };
+    CUDA_TRY(c, cudaEventRecord(c->tb_entry, c->stream));
+    for (int s = 0; s < k; ++s)
+        CUDA_TRY(c, cudaStreamWaitEvent(c->tb_stream[s], c->tb_entry, 0));
+    for (int blk = 0; blk < m; ++blk) {
+        for (int dg = 0; dg < nb + k - 1; ++dg)
+            for (int s = 0; s < k; ++s) {
+                const int b = dg - s;
+                if (b < 0 || b >= nb)
+                    continue;
+                cudaStream_t st = c->tb_stream[s];
+                const int nxt = std::min(b + 1, nb - 1);
+                if (s > 0)
+                    CUDA_TRY(c, cudaStreamWaitEvent(st, ev(s - 1, nxt), 0));
+                else if (blk > 0)
+                    CUDA_TRY(c, cudaStreamWaitEvent(st, ev(k - 1, nxt), 0));
+                StepArgs a = base_args(c);
+                const int set = (c->cur + s) & 1;
+                a.t = c->t + s;
+                a.zbase = b * c->tb_band;
+                a.zend = b == nb - 1 ? c->g.nz : (b + 1) * c->tb_band;
+                a.zchunk = a.zend - a.zbase;
+                a.p_in = c->p[set];
+                a.p_out = c->p[set ^ 1];
+                for (int d = 0; d < 3; ++d) {
+                    a.v_in[d] = c->v[d][set];
+                    a.v_out[d] = c->v[d][set ^ 1];
+                    a.psiv_in[d] = c->psiv[d][set];
+                    a.psiv_out[d] = c->psiv[d][set ^ 1];
+                }
+                CUDA_TRY(c, launch_step(c, a, set, st));
+                CUDA_TRY(c, cudaEventRecord(ev(s, b), st));
+            }
+        c->cur = (c->cur + k) & 1;
+        c->t += k;
+    }
+    // the last step's final band comes after every other launch of the run
+    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, ev(k - 1, nb - 1), 0));
+    return FDTD_OK;
+}
+
 int launch_one_step(fdtd_ctx *c, bool record, float *s_tape, float *const slab_tape[3])
 {
     StepArgs a = base_args(c);
@@ -410,7 +527,7 @@ int launch_one_step(fdtd_ctx *c, bool record, float *s_tape, float *const slab_t
     if (!record)
         a.traces = nullptr;
     a.s_tape = s_tape;
-    CUDA_TRY(c, launch_step(c, a, s));
+    CUDA_TRY(c, launch_step(c, a, s, c->stream));
     c->cur ^= 1;
     c->t += 1;
     return FDTD_OK;
@@ -619,6 +736,10 @@ int fdtd_create(const fdtd_desc *desc, void *workspace, size_t workspace_bytes, 
         delete c;
         return FDTD_ECUDA;
     }
+    if ((st = make_tblock(c)) != FDTD_OK) {
+        free_ctx(c);
+        return st;
+    }
     *out = c;
     return FDTD_OK;
 }
@@ -627,7 +748,7 @@ int fdtd_destroy(fdtd_ctx *c)
 {
     if (!c)
         return FDTD_EINVAL;
-    delete c;
+    free_ctx(c);
     return FDTD_OK;
 }
 
@@ -800,14 +921,36 @@ int fdtd_step_n(fdtd_ctx *c, int n)
         return fail(c, FDTD_ESTATE, "fdtd_set_cpml has not been called");
     if (fault_is("launch"))
         return fail(c, FDTD_ECUDA, "injected launch failure (FDTD_FAULT=launch)");
-    const int C = c->d.checkpoint_every;
-    for (int i = 0; i < n; ++i) {
-        if (C > 0 && c->t % C == 0 && c->t / C < c->ncp) {
-            int st = copy_state(c, c->t / C, true);
+    const int k = c->d.tblock_k;
+    for (int i = 0; i < n;) {
+        if (needs_ckpt(c, c->t)) {
+            int st = copy_state(c, c->t / c->d.checkpoint_every, true);
             if (st)
                 return st;
         }
-        int st = launch_one_step(c, true, nullptr, nullptr);
+        // as many whole blocks of k steps as fit before n and before the next
+        // checkpoint; a checkpoint inside a block leaves that block to single steps
+        int m = 0;
+        if (k > 1)
+            while (i + (m + 1) * k <= n) {
+                const int t0 = c->t + m * k;
+                bool inside = false;
+                for (int j = 1; j < k; ++j)
+                    inside = inside || needs_ckpt(c, t0 + j);
+                if (inside)
+                    break;
+                ++m;
+                if (needs_ckpt(c, t0 + k))
+                    break;
+            }
+        int st;
+        if (m > 0) {
+            st = launch_blocks(c, m);
+            i += m * k;
+        } else {
+            st = launch_one_step(c, true, nullptr, nullptr);
+            ++i;
+        }
         if (st)
             return st;
     }

@@ -276,6 +276,7 @@ __host__ __device__ __forceinline__ void x_slab_layout(int nx, int lo, int hi, i
 struct StepArgs {
     Geom g;
     int tiles_x, zchunk;
+    int zbase, zend;                // z range of this launch: [zbase, zend), cut into zchunk planes per CTA
     int t;                          // time index of this step
     const void *p_in;
     void *p_out;
@@ -348,5 +349,12 @@ struct fdtd_ctx {
     // adjoint (FP32, built when checkpoint slots exist): lam_p 40x40 and
     // 32x32, kdt 40x40, lam_v_x 40x32, lam_v_y 32x40, lam_v_z 32x32
     CUtensorMap amaps[6];
+    // temporal blocking (tblock_k > 1): one stream per step of a block, one
+    // event per (step, z band); band b covers [b * tb_band, (b + 1) * tb_band)
+    // and the last band runs to nz
+    int tb_nb, tb_band;
+    cudaStream_t tb_stream[4];
+    cudaEvent_t *tb_ev;     // [tblock_k][tb_nb]
+    cudaEvent_t tb_entry;
     char last_error[256];
 };

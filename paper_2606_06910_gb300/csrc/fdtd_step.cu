@@ -231,8 +231,8 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
     const int tx = tid % (TX / 4), ty = tid / (TX / 4);
     const int tile = blockIdx.x;
     const int x0 = (tile % A.tiles_x) * TX, y0 = (tile / A.tiles_x) * TY;
-    const int z0 = blockIdx.y * A.zchunk;
-    const int z1 = min(G.nz, z0 + A.zchunk);
+    const int z0 = A.zbase + blockIdx.y * A.zchunk;
+    const int z1 = min(A.zend, z0 + A.zchunk);
     const int shot = blockIdx.z;
     const int gx = x0 + 4 * tx, gy = y0 + ty;
     const int niter = z1 - z0 + 8;
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
 }
 
 template <typename T>
-static cudaError_t launch_step_t(const fdtd_ctx *c, const StepArgs &a, int set)
+static cudaError_t launch_step_t(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream)
 {
     using L = StageLayout<T>;
     static bool attr_done = false;
@@ -630,21 +630,23 @@ static cudaError_t launch_step_t(const fdtd_ctx *c, const StepArgs &a, int set)
             return e;
         attr_done = true;
     }
-    dim3 grid(c->tiles_x * c->tiles_y, c->nzchunks, c->d.nshots);
-    fdtd_step_kernel<T><<<grid, NTHREADS, L::SMEM, c->stream>>>(c->maps[set][0], c->maps[set][1], c->maps[set][2],
-                                                                 c->maps[set][3], c->maps[set][4], c->mapK, a);
+    dim3 grid(c->tiles_x * c->tiles_y, (a.zend - a.zbase + a.zchunk - 1) / a.zchunk, c->d.nshots);
+    fdtd_step_kernel<T><<<grid, NTHREADS, L::SMEM, stream>>>(c->maps[set][0], c->maps[set][1], c->maps[set][2],
+                                                              c->maps[set][3], c->maps[set][4], c->mapK, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const fdtd_ctx *c, const StepArgs &a, int set)
+// One step over z in [a.zbase, a.zend) on `stream`; `set` is the ping-pong
+// set holding the input state.
+cudaError_t launch_step(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream)
 {
     switch (c->d.storage) {
     case FDTD_F16:
-        return launch_step_t<__half>(c, a, set);
+        return launch_step_t<__half>(c, a, set, stream);
     case FDTD_BF16:
-        return launch_step_t<__nv_bfloat16>(c, a, set);
+        return launch_step_t<__nv_bfloat16>(c, a, set, stream);
     default:
-        return launch_step_t<float>(c, a, set);
+        return launch_step_t<float>(c, a, set, stream);
     }
 }
 

@@ -47,7 +47,7 @@ class Fdtd:
     """
 
     def __init__(self, shape, h, dt, *, nshots=1, cpml_cells=0, storage="f32", nt_max=1,
-                 nrec_max=0, checkpoint_every=0, cpml_grad=False, device=None, stream=None):
+                 nrec_max=0, checkpoint_every=0, cpml_grad=False, tblock_k=1, device=None, stream=None):
         self.lib = _lib.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda")
         if self.device.type != "cuda":
@@ -70,7 +70,8 @@ class Fdtd:
         for i, c in enumerate(self.cells):
             d.cpml_cells[i] = c
         d.storage = STORAGE[storage]
-        d.tblock_k = 1
+        d.tblock_k = int(tblock_k)
+        self.tblock_k = int(tblock_k)
         d.nt_max = self.nt_max
         d.nrec_max = int(nrec_max)
         d.checkpoint_every = int(checkpoint_every)

@@ -78,12 +78,20 @@ def test_memory_model_matches_tab14():
 
 @pytest.mark.parametrize("bad", [
     dict(nx=0), dict(h=0.0), dict(dt=-1.0), dict(cells=(40, 40, 0, 0, 0, 0)), dict(storage=7),
-    dict(tblock_k=3), dict(nt_max=0), dict(nshots=0), dict(nshots=2000), dict(nrec_max=-1),
+    dict(tblock_k=3), dict(tblock_k=0), dict(tblock_k=8), dict(nt_max=0), dict(nshots=0), dict(nshots=2000), dict(nrec_max=-1),
     dict(checkpoint_every=-2), dict(cpml_grad=1),
 ])
 def test_invalid_descriptors_rejected(lib, bad):
     st, _ = _bytes(lib, _desc(**bad))
     assert st == _lib.EINVAL
+
+
+def test_temporal_blocking_needs_no_extra_workspace(lib):
+    # k = 2, 4 run in the two ping-pong sets that single steps use
+    st1, b1 = _bytes(lib, _desc(tblock_k=1))
+    for k in (2, 4):
+        st, b = _bytes(lib, _desc(tblock_k=k))
+        assert st == _lib.OK and b == b1
 
 
 def test_adjoint_needs_fp32(lib):
