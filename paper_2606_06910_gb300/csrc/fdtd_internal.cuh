@@ -59,6 +59,12 @@ struct Io<float> {
     {
         *reinterpret_cast<float4 *>(p) = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
     }
+    // store that is not read again soon (L2 evict-first)
+    static __device__ __forceinline__ void st4s(float *p, const F4 &v)
+    {
+        __stcs(reinterpret_cast<float4 *>(p), make_float4(v.v[0], v.v[1], v.v[2], v.v[3]));
+    }
+    static __device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
     static __device__ __forceinline__ float ld1(const float *p) { return *p; }
     static __device__ __forceinline__ void st1(float *p, float v) { *p = v; }
 };
@@ -80,14 +86,20 @@ struct Io<__half> {
     {
         return from_u2(__ldg(reinterpret_cast<const uint2 *>(p)));
     }
-    static __device__ __forceinline__ void st4(__half *p, const F4 &v)
+    static __device__ __forceinline__ uint2 to_u2(const F4 &v)
     {
         __half2 a = __floats2half2_rn(v.v[0], v.v[1]);
         __half2 b = __floats2half2_rn(v.v[2], v.v[3]);
         uint2 u;
         u.x = *reinterpret_cast<uint32_t *>(&a);
         u.y = *reinterpret_cast<uint32_t *>(&b);
-        *reinterpret_cast<uint2 *>(p) = u;
+        return u;
+    }
+    static __device__ __forceinline__ void st4(__half *p, const F4 &v) { *reinterpret_cast<uint2 *>(p) = to_u2(v); }
+    static __device__ __forceinline__ void st4s(__half *p, const F4 &v) { __stcs(reinterpret_cast<uint2 *>(p), to_u2(v)); }
+    static __device__ __forceinline__ float2 ld2(const __half *p)
+    {
+        return __half22float2(*reinterpret_cast<const __half2 *>(p));
     }
     static __device__ __forceinline__ float ld1(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st1(__half *p, float v) { *p = __float2half_rn(v); }
@@ -110,14 +122,26 @@ struct Io<__nv_bfloat16> {
     {
         return from_u2(__ldg(reinterpret_cast<const uint2 *>(p)));
     }
-    static __device__ __forceinline__ void st4(__nv_bfloat16 *p, const F4 &v)
+    static __device__ __forceinline__ uint2 to_u2(const F4 &v)
     {
         __nv_bfloat162 a = __floats2bfloat162_rn(v.v[0], v.v[1]);
         __nv_bfloat162 b = __floats2bfloat162_rn(v.v[2], v.v[3]);
         uint2 u;
         u.x = *reinterpret_cast<uint32_t *>(&a);
         u.y = *reinterpret_cast<uint32_t *>(&b);
-        *reinterpret_cast<uint2 *>(p) = u;
+        return u;
+    }
+    static __device__ __forceinline__ void st4(__nv_bfloat16 *p, const F4 &v)
+    {
+        *reinterpret_cast<uint2 *>(p) = to_u2(v);
+    }
+    static __device__ __forceinline__ void st4s(__nv_bfloat16 *p, const F4 &v)
+    {
+        __stcs(reinterpret_cast<uint2 *>(p), to_u2(v));
+    }
+    static __device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p)
+    {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
     }
     static __device__ __forceinline__ float ld1(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st1(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
@@ -181,6 +205,41 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
         "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// L2 eviction policies for the cache-hinted TMA loads below
+__device__ __forceinline__ uint64_t l2_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ void tma_load_4d_hint(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                                 int c2, int c3, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d_hint(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                                 int c2, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
 

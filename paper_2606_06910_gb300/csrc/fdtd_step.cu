@@ -30,8 +30,20 @@
 #ifndef FDTD_PREFETCH
 #define FDTD_PREFETCH 1
 #endif
+// L2 policy bits: 1 = outputs stored evict-first, 2 = the z-queue plane of p
+// (read again 8 planes later) loaded evict-last, 4 = v_z and K (read once)
+// loaded evict-first
+#ifndef FDTD_L2HINT
+#define FDTD_L2HINT 0
+#endif
+// unroll factor of the z march (lets the compiler rename the queue registers)
+#ifndef FDTD_UNROLL
+#define FDTD_UNROLL 1
+#endif
 
 namespace fdtd {
+
+constexpr int kZUnroll = FDTD_UNROLL;
 
 template <typename T>
 struct StageLayout {
@@ -156,6 +168,48 @@ __device__ __forceinline__ V4 dx4(const V4 &u, const V4 &v, const V4 &w, const C
     return r;
 }
 
+// The same two operations on one pair of nodes, with the operation order of
+// the first pair of dnb / dx4, so that a recomputed halo pair equals what the
+// neighbouring tile computes for its own nodes, bit for bit.
+__device__ __forceinline__ float2 dnb2(const float2 *m, const float2 *p, const Coef &C)
+{
+    float2 r = mul2(C.cp[0], p[0]);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        if (l > 0)
+            r = fma2(C.cp[l], p[l], r);
+        r = fma2(C.cn[l], m[l], r);
+    }
+    return r;
+}
+
+// x derivative of the pair at offsets 4, 5 of P0..P4 (offsets 0..9)
+__device__ __forceinline__ float2 dx2(float2 P0, float2 P1, float2 P2, float2 P3, float2 P4, const Coef &C)
+{
+    float2 r = mul2(C.cp[1], P3);
+    r = fma2(C.cn[1], P1, r);
+    r = fma2(C.cp[3], P4, r);
+    r = fma2(C.cn[3], P0, r);
+    const float c1 = C.cp[0].x, c3 = C.cp[2].x;
+    r.x = fmaf(c1, P2.y - P1.y, r.x);
+    r.y = fmaf(c1, P3.x - P2.x, r.y);
+    r.x = fmaf(c3, P3.y - P0.y, r.x);
+    r.y = fmaf(c3, P4.x - P1.x, r.y);
+    return r;
+}
+
+__device__ __forceinline__ void cpml2(float2 &g, float2 psi, float2 b, float2 a, float2 k)
+{
+    const float2 pn = fma2(b, psi, mul2(a, g));
+    g = fma2(k, g, pn);
+}
+
+template <typename T>
+__device__ __forceinline__ float2 lds2(const unsigned char *base, int elem)
+{
+    return Io<T>::ld2(reinterpret_cast<const T *>(base) + elem);
+}
+
 // One CPML update of 4 nodes: psi' = b psi + a g ; g' = kinv g + psi'.
 __device__ __forceinline__ V4 cpml4(V4 &g, const V4 &psi, const V4 &b, const V4 &a, const V4 &k)
 {
@@ -171,6 +225,16 @@ __device__ __forceinline__ V4 splat4(float s) { return V4{make_float2(s, s), mak
 
 template <typename T>
 __device__ __forceinline__ V4 ldg_v4(const T *p) { return to_v4(Io<T>::ld4(p)); }
+
+// store of a step output (not read again within this step)
+template <typename T>
+__device__ __forceinline__ void st_out(T *p, const F4 &v)
+{
+    if (FDTD_L2HINT & 1)
+        Io<T>::st4s(p, v);
+    else
+        Io<T>::st4(p, v);
+}
 
 // tape (g, psi_old) of 4 nodes into slots [idx*4 + off, +1]
 __device__ __forceinline__ void tape4(float *tape, long long idx, int off, const V4 &g, const V4 &psi)
@@ -287,21 +351,21 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
     const bool own_x = G.w[0] > 0 && gy < G.ny && gx < G.nx && (gx < G.lo[0] || gx + 3 >= G.nx - G.hi[0]);
     const bool own_y = G.w[1] > 0 && row_ok && in_slab(gy, G.ny, G.lo[1], G.hi[1]);
 
-    // halo task of this thread (warps 4-5: y halo rows, warps 6-7: x halo)
-    const int hy_task = tid - NTHREADS / 2;
-    const int hx_task = tid - (NTHREADS / 2 + 8 * (TX / 4));
-    const bool do_yhalo = hy_task >= 0 && hy_task < 8 * (TX / 4);
-    const bool do_xhalo = hx_task >= 0 && hx_task < 2 * TY;
-    const int yh_r = do_yhalo ? hy_task / (TX / 4) : 0, yh_c = do_yhalo ? hy_task % (TX / 4) : 0;
+    // halo task of this thread: one pair of nodes.  Threads 0..127: the y
+    // halo (8 rows x 16 pairs), threads 128..255: the x halo (32 rows x 2
+    // pairs on each side).  Every thread then computes 1.5 vectors of v'.
+    static_assert(TX == 32 && TY == 32 && NTHREADS == 256, "halo pairs assume 32x32 tiles and 256 threads");
+    const bool do_yhalo = tid < 128;
+    const int yh_r = (tid / 16) & 7;
     const int yh_y = yh_r < 4 ? y0 - 4 + yh_r : y0 + TY + (yh_r - 4);
-    const int yh_x = x0 + 4 * yh_c;
-    const int xh_r = do_xhalo ? (hx_task >> 1) : 0;
-    const int xh_x = (do_xhalo && (hx_task & 1)) ? x0 + TX : x0 - 4;
-    const int xh_y = y0 + xh_r;
+    const int yh_x = x0 + 2 * (tid % 16);
+    const int xh_k = tid & 3;
+    const int xh_x = xh_k < 2 ? x0 - 4 + 2 * xh_k : x0 + TX + 2 * (xh_k - 2);
+    const int xh_y = y0 + ((tid - 128) >> 2);
     const bool yh_in = yh_y >= 0 && yh_y < G.ny;
     const bool halo_psi_y = do_yhalo && G.w[1] > 0 && yh_in && yh_x < G.nxp && in_slab(yh_y, G.ny, G.lo[1], G.hi[1]);
-    const bool halo_psi_x = do_xhalo && G.w[0] > 0 && xh_y < G.ny && xh_x >= 0 && xh_x < G.nx &&
-                            (xh_x < G.lo[0] || xh_x + 3 >= G.nx - G.hi[0]);
+    const bool halo_psi_x = !do_yhalo && G.w[0] > 0 && xh_y < G.ny && xh_x >= 0 && xh_x < G.nx &&
+                            (xh_x < G.lo[0] || xh_x + 1 >= G.nx - G.hi[0]);
     const bool slab_thread = own_x || own_y || halo_psi_x || halo_psi_y;
 
     // source of this shot
@@ -330,6 +394,8 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
     }
     __syncthreads();
 
+    const uint64_t pol_first = (FDTD_L2HINT & 4) ? l2_evict_first() : 0;
+    const uint64_t pol_last = (FDTD_L2HINT & 2) ? l2_evict_last() : 0;
     // Issue the loads of iteration `it` into its stage (thread 0 only).
     auto issue = [&](int it) {
         const int t = z0 - 8 + it;
@@ -343,15 +409,26 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
         bytes += vz_on ? L::VZ_BYTES : 0;
         bytes += main_on ? (L::P_BYTES + L::VX_BYTES + L::VY_BYTES + L::K_BYTES) : 0;
         mbar_arrive_expect_tx(b, bytes);
-        if (q_on)
-            tma_load_4d(S + L::OFF_PQ, &mPq, b, x0, y0, t + 8, shot);
-        if (vz_on)
-            tma_load_4d(S + L::OFF_VZ, &mVZ, b, x0, y0, t + 4, shot);
+        if (q_on) {
+            if (FDTD_L2HINT & 2)
+                tma_load_4d_hint(S + L::OFF_PQ, &mPq, b, x0, y0, t + 8, shot, pol_last);
+            else
+                tma_load_4d(S + L::OFF_PQ, &mPq, b, x0, y0, t + 8, shot);
+        }
+        if (vz_on) {
+            if (FDTD_L2HINT & 4)
+                tma_load_4d_hint(S + L::OFF_VZ, &mVZ, b, x0, y0, t + 4, shot, pol_first);
+            else
+                tma_load_4d(S + L::OFF_VZ, &mVZ, b, x0, y0, t + 4, shot);
+        }
         if (main_on) {
             tma_load_4d(S + L::OFF_P, &mP, b, x0 - 8, y0 - 8, t, shot);
             tma_load_4d(S + L::OFF_VX, &mVX, b, x0 - 8, y0, t, shot);
             tma_load_4d(S + L::OFF_VY, &mVY, b, x0, y0 - 4, t, shot);
-            tma_load_3d(S + L::OFF_K, &mK, b, x0, y0, t);
+            if (FDTD_L2HINT & 4)
+                tma_load_3d_hint(S + L::OFF_K, &mK, b, x0, y0, t, pol_first);
+            else
+                tma_load_3d(S + L::OFF_K, &mK, b, x0, y0, t);
         }
     };
     if (tid == 0)
@@ -371,6 +448,7 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
     pq[8] = v4zero();
     vzq[8] = v4zero();
 
+#pragma unroll kZUnroll
     for (int it = 0; it < niter; ++it) {
         const int t = z0 - 8 + it;
         const int zv = t + 4;
@@ -426,11 +504,11 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
                         tape4(stape[2], izv, 0, gz, psvz);
                     const V4 pn = cpml4(gz, psvz, b, a, k);
                     if (owned)
-                        Io<T>::st4(psiv_out[2] + izv, to_f4(pn));
+                        st_out(psiv_out[2] + izv, to_f4(pn));
                 }
                 vzn = fma4(ndtr, gz, lds<T>(S + L::OFF_VZ, ty * TX + 4 * tx));
                 if (owned && row_ok)
-                    Io<T>::st4(v_out[2] + (long long)zv * G.plane + rowofs, to_f4(vzn));
+                    st_out(v_out[2] + (long long)zv * G.plane + rowofs, to_f4(vzn));
             }
             return vzn;
         };
@@ -451,13 +529,13 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
                     if (stape[0])
                         tape4(stape[0], ix, 0, g, psvx);
                     const V4 pn = cpml4(g, psvx, ldsf(&sCx[0][cx]), ldsf(&sCx[1][cx]), ldsf(&sCx[2][cx]));
-                    Io<T>::st4(psiv_out[0] + ix, to_f4(pn));
+                    st_out(psiv_out[0] + ix, to_f4(pn));
                 }
                 V4 vn = fma4(ndtr, g, lds<T>(S + L::OFF_VX, ty * L::VXW + 4 * tx + 8));
                 if (!full_tile)
                     vn = mul4(vn, mask);
                 if (row_ok)
-                    Io<T>::st4(v_out[0] + pofs, to_f4(vn));
+                    st_out(v_out[0] + pofs, to_f4(vn));
                 stsf(svx + ty * L::SVXW + 4 * tx + 4, vn);
             }
             // ---- v'_y, own nodes
@@ -476,53 +554,49 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
                     if (stape[1])
                         tape4(stape[1], iy, 0, g, psvy);
                     const V4 pn = cpml4(g, psvy, splat4(sCy[0][ty + 4]), splat4(sCy[1][ty + 4]), splat4(sCy[2][ty + 4]));
-                    Io<T>::st4(psiv_out[1] + iy, to_f4(pn));
+                    st_out(psiv_out[1] + iy, to_f4(pn));
                 }
                 V4 vn = fma4(ndtr, g, lds<T>(S + L::OFF_VY, (ty + 4) * TX + 4 * tx));
                 if (!full_tile)
                     vn = mul4(vn, mask);
                 if (row_ok)
-                    Io<T>::st4(v_out[1] + pofs, to_f4(vn));
+                    st_out(v_out[1] + pofs, to_f4(vn));
                 stsf(svy + (ty + 4) * TX + 4 * tx, vn);
             }
-            // ---- halos (recomputed, not stored)
+            // ---- halos (recomputed, not stored): one pair of nodes per thread
             if (do_yhalo) {
-                const int ly = yh_y - y0 + 8, lx = 4 * yh_c + 8;
-                V4 m[4], p[4];
+                const int ly = yh_y - y0 + 8, lx = yh_x - x0 + 8;
+                float2 m[4], p[4];
 #pragma unroll
                 for (int l = 1; l <= 4; ++l) {
-                    m[l - 1] = lds<T>(Sp, (ly - l) * L::PW + lx);
-                    p[l - 1] = lds<T>(Sp, (ly + l) * L::PW + lx);
+                    m[l - 1] = lds2<T>(Sp, (ly - l) * L::PW + lx);
+                    p[l - 1] = lds2<T>(Sp, (ly + l) * L::PW + lx);
                 }
-                V4 g = dnb(m, p, C);
+                float2 g = dnb2(m, p, C);
+                const int r = yh_y - y0 + 4;
                 if (halo_psi_y) {
-                    const int r = yh_y - y0 + 4;
-                    const V4 psh = ldg_v4(psiv_in[1] + slab_index(G, 1, t, yh_y, yh_x));
-                    cpml4(g, psh, splat4(sCy[0][r]), splat4(sCy[1][r]), splat4(sCy[2][r]));
+                    const float2 psh = Io<T>::ld2(psiv_in[1] + slab_index(G, 1, t, yh_y, yh_x));
+                    cpml2(g, psh, make_float2(sCy[0][r], sCy[0][r]), make_float2(sCy[1][r], sCy[1][r]),
+                          make_float2(sCy[2][r], sCy[2][r]));
                 }
-                V4 vn = fma4(ndtr, g, lds<T>(S + L::OFF_VY, (yh_y - y0 + 4) * TX + 4 * yh_c));
-                if (!full_tile || !yh_in) {
-                    F4 f = to_f4(vn);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        f.v[i] = (yh_in && yh_x + i < G.nx) ? f.v[i] : 0.f;
-                    vn = to_v4(f);
-                }
-                stsf(svy + (yh_y - y0 + 4) * TX + 4 * yh_c, vn);
-            } else if (do_xhalo) {
-                const int lrow = (xh_r + 8) * L::PW, lx = xh_x - x0 + 8;
-                V4 g = dx4(lds<T>(Sp, lrow + lx - 4), lds<T>(Sp, lrow + lx), lds<T>(Sp, lrow + lx + 4), C);
+                float2 vn = fma2(ndtr, g, lds2<T>(S + L::OFF_VY, r * TX + (yh_x - x0)));
+                vn.x = (yh_in && yh_x < G.nx) ? vn.x : 0.f;
+                vn.y = (yh_in && yh_x + 1 < G.nx) ? vn.y : 0.f;
+                *reinterpret_cast<float2 *>(svy + r * TX + (yh_x - x0)) = vn;
+            } else {
+                const int lrow = (xh_y - y0 + 8) * L::PW, lx = xh_x - x0 + 8;
+                float2 g = dx2(lds2<T>(Sp, lrow + lx - 4), lds2<T>(Sp, lrow + lx - 2), lds2<T>(Sp, lrow + lx),
+                               lds2<T>(Sp, lrow + lx + 2), lds2<T>(Sp, lrow + lx + 4), C);
+                const int cx = xh_x - x0 + 4;
                 if (halo_psi_x) {
-                    const int cx = xh_x - x0 + 4;
-                    const V4 psh = ldg_v4(psiv_in[0] + slab_index(G, 0, t, xh_y, xh_x));
-                    cpml4(g, psh, ldsf(&sCx[0][cx]), ldsf(&sCx[1][cx]), ldsf(&sCx[2][cx]));
+                    const float2 psh = Io<T>::ld2(psiv_in[0] + slab_index(G, 0, t, xh_y, xh_x));
+                    cpml2(g, psh, *reinterpret_cast<const float2 *>(&sCx[0][cx]),
+                          *reinterpret_cast<const float2 *>(&sCx[1][cx]), *reinterpret_cast<const float2 *>(&sCx[2][cx]));
                 }
-                V4 vn = fma4(ndtr, g, lds<T>(S + L::OFF_VX, xh_r * L::VXW + lx));
-                F4 f = to_f4(vn);
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    f.v[i] = (xh_y < G.ny && xh_x + i >= 0 && xh_x + i < G.nx) ? f.v[i] : 0.f;
-                stsf(svx + xh_r * L::SVXW + (xh_x - x0 + 4), to_v4(f));
+                float2 vn = fma2(ndtr, g, lds2<T>(S + L::OFF_VX, (xh_y - y0) * L::VXW + lx));
+                vn.x = (xh_y < G.ny && xh_x >= 0 && xh_x < G.nx) ? vn.x : 0.f;
+                vn.y = (xh_y < G.ny && xh_x + 1 >= 0 && xh_x + 1 < G.nx) ? vn.y : 0.f;
+                *reinterpret_cast<float2 *>(svx + (xh_y - y0) * L::SVXW + cx) = vn;
             }
         }
 
@@ -557,7 +631,7 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
                 if (stape[0])
                     tape4(stape[0], ix, 2, hx4, pspx);
                 const V4 pn = cpml4(hx4, pspx, ldsf(&sCx[0][cx]), ldsf(&sCx[1][cx]), ldsf(&sCx[2][cx]));
-                Io<T>::st4(psip[0] + ix, to_f4(pn));
+                st_out(psip[0] + ix, to_f4(pn));
             }
             if (own_y) {
                 const long long iy = slab_index(G, 1, t, gy, gx);
@@ -565,7 +639,7 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
                 if (stape[1])
                     tape4(stape[1], iy, 2, hy4, pspy);
                 const V4 pn = cpml4(hy4, pspy, splat4(sCy[0][ty + 4]), splat4(sCy[1][ty + 4]), splat4(sCy[2][ty + 4]));
-                Io<T>::st4(psip[1] + iy, to_f4(pn));
+                st_out(psip[1] + iy, to_f4(pn));
             }
             if (zs_p) {
                 const long long izp = slab_index(G, 2, t, gy, gx);
@@ -574,7 +648,7 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
                     tape4(stape[2], izp, 2, hz4, pspz);
                 const V4 pn = cpml4(hz4, pspz, splat4(__ldg(A.cb[2] + t)), splat4(__ldg(A.ca[2] + t)),
                                     splat4(__ldg(A.ck[2] + t)));
-                Io<T>::st4(psip[2] + izp, to_f4(pn));
+                st_out(psip[2] + izp, to_f4(pn));
             }
             // nkdt holds -dt K / vscale (zero beyond the grid)
             const V4 nkd = ldsf(reinterpret_cast<const float *>(S + L::OFF_K) + ty * TX + 4 * tx);
@@ -589,7 +663,7 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
             }
             if (row_ok) {
                 const long long o = (long long)t * G.plane + rowofs;
-                Io<T>::st4(reinterpret_cast<T *>(A.p_out) + fofs + o, to_f4(pn));
+                st_out(reinterpret_cast<T *>(A.p_out) + fofs + o, to_f4(pn));
                 if (A.s_tape)
                     stsf(A.s_tape + fofs + o, sb);
             }
