@@ -287,16 +287,27 @@ void choose_zchunk(fdtd_ctx *c)
     // 256^3 x 16 shots, 512^3 and 1024^3 this beats the wave count above.
     const int target = c->d.storage == FDTD_F32 ? 48 : 96;
     const int kt = (nz + target - 1) / target;
-    if (per_z * kt >= 2 * slots) {
+    const bool large = per_z * kt >= 2 * slots;
+    if (large)
         best = (nz + kt - 1) / kt;
-    }
-    if (const char *e = getenv("FDTD_ZCHUNK")) {
-        const int v = atoi(e);
-        if (v > 0)
-            best = std::min(v, nz);
-    }
+    c->zmid0 = 0;
+    c->zmid1 = nz;
+    const char *env = getenv("FDTD_ZCHUNK");
+    if (env && atoi(env) > 0)
+        best = std::min(atoi(env), nz);
     c->zchunk = best;
     c->nzchunks = (nz + best - 1) / best;
+    c->zchunk_mid = best;
+    // Forward steps on large grids: the planes that meet a z slab, with the
+    // 4-plane reach of v_z, get a chunk of their own at each end, so that the
+    // chunks in between run the step kernel's interior form.
+    const int e1 = c->g.lo[2] + 4, e2 = nz - c->g.hi[2] - 4;
+    if (large && !(env && atoi(env) > 0) && e2 - e1 >= target) {
+        const int km = (e2 - e1 + target - 1) / target;
+        c->zmid0 = e1;
+        c->zmid1 = e2;
+        c->zchunk_mid = (e2 - e1 + km - 1) / km;
+    }
 }
 
 void host_profile(int n, int lo, int hi, double h, double dt, double R, double kmax, double afrac, int q, double cref,
@@ -424,9 +435,11 @@ StepArgs base_args(const fdtd_ctx *c)
     memset(&a, 0, sizeof(a));
     a.g = c->g;
     a.tiles_x = c->tiles_x;
-    a.zchunk = c->zchunk;
+    a.zchunk = c->zchunk_mid;
     a.zbase = 0;
     a.zend = c->g.nz;
+    a.zmid0 = c->zmid0;
+    a.zmid1 = c->zmid1;
     const int nmax = nmax_of(c->g);
     for (int d = 0; d < 3; ++d) {
         a.cb[d] = c->coef + (d * 3 + 0) * nmax;
@@ -491,6 +504,8 @@ int launch_blocks(fdtd_ctx *c, int m)
                 a.zbase = b * c->tb_band;
                 a.zend = b == nb - 1 ? c->g.nz : (b + 1) * c->tb_band;
                 a.zchunk = a.zend - a.zbase;
+                a.zmid0 = a.zbase;
+                a.zmid1 = a.zend;
                 a.p_in = c->p[set];
                 a.p_out = c->p[set ^ 1];
                 for (int d = 0; d < 3; ++d) {

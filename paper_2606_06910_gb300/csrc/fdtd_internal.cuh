@@ -335,7 +335,9 @@ __host__ __device__ __forceinline__ void x_slab_layout(int nx, int lo, int hi, i
 struct StepArgs {
     Geom g;
     int tiles_x, zchunk;
-    int zbase, zend;                // z range of this launch: [zbase, zend), cut into zchunk planes per CTA
+    int zbase, zend;                // z range of this launch: [zbase, zend)
+    int zmid0, zmid1;               // chunks: [zbase, zmid0) if not empty, then zchunk planes per CTA
+                                    // over [zmid0, zmid1), then [zmid1, zend) if not empty
     int t;                          // time index of this step
     const void *p_in;
     void *p_out;
@@ -368,7 +370,8 @@ struct fdtd_ctx {
     cudaStream_t stream;
     fdtd::Geom g;
     int es;                 // bytes per stored element
-    int tiles_x, tiles_y, zchunk, nzchunks;
+    int tiles_x, tiles_y, zchunk, nzchunks;   // uniform z-chunks (adjoint kernels)
+    int zmid0, zmid1, zchunk_mid;             // forward step chunks (see StepArgs::zmid0)
     float vscale;           // stored velocity = vscale * v (impedance scaling for 16-bit)
     float sscale;           // every stored field is multiplied by sscale (2^10 for FP16, else 1)
     float c_max, c_min;

@@ -273,30 +273,50 @@ __device__ __forceinline__ void zblock(V4 (&pq)[9], V4 (&vzq)[9], const V4 &pnew
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
-    fdtd_step_kernel(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mPq,
-                     const __grid_constant__ CUtensorMap mVX, const __grid_constant__ CUtensorMap mVY,
-                     const __grid_constant__ CUtensorMap mVZ, const __grid_constant__ CUtensorMap mK,
-                     const StepArgs A)
+// z range of chunk y of a launch (see StepArgs::zmid0).  The zchunk-plane
+// chunks of [zmid0, zmid1) come first, the shorter end chunks last, so that
+// the long chunks start in the first waves.
+__host__ __device__ __forceinline__ void chunk_range(const StepArgs &A, int y, int *z0, int *z1)
+{
+    const int nmid = (A.zmid1 - A.zmid0 + A.zchunk - 1) / A.zchunk;
+    if (y < nmid) {
+        *z0 = A.zmid0 + y * A.zchunk;
+        *z1 = min(A.zmid1, *z0 + A.zchunk);
+    } else if (y == nmid && A.zmid0 > A.zbase) {
+        *z0 = A.zbase;
+        *z1 = A.zmid0;
+    } else {
+        *z0 = A.zmid1;
+        *z1 = A.zend;
+    }
+}
+
+__host__ __device__ __forceinline__ int chunk_count(const StepArgs &A)
+{
+    return (A.zmid0 > A.zbase ? 1 : 0) + (A.zmid1 - A.zmid0 + A.zchunk - 1) / A.zchunk + (A.zend > A.zmid1 ? 1 : 0);
+}
+
+// The body of one CTA.  kEdge = false is the interior form: the CTA's tile
+// with its 4-node x / y halo and its z range with 4 planes either side lie
+// inside the grid and outside every CPML slab, so it needs no memory
+// variables, no coefficient tables and no masks at the grid edge.  The same
+// arithmetic in the same order runs in both forms.
+template <typename T, bool kEdge>
+__device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorMap &mPq, const CUtensorMap &mVX,
+                                          const CUtensorMap &mVY, const CUtensorMap &mVZ, const CUtensorMap &mK,
+                                          const StepArgs &A, int z0, int z1, unsigned char *smem,
+                                          float (*sCx)[TX + 8], float (*sCy)[TY + 8])
 {
     using L = StageLayout<T>;
-    extern __shared__ __align__(1024) unsigned char smem[];
     float *svx = reinterpret_cast<float *>(smem + NSTAGE * L::BYTES);
     float *svy = svx + L::SVX_FLOATS;
     uint64_t *bar = reinterpret_cast<uint64_t *>(svy + L::SVY_FLOATS);
-    // CPML coefficients (b, a, 1/kappa) of the tile's x range [x0-4, x0+TX+4)
-    // and y range [y0-4, y0+TY+4); 0, 0, 1 outside the slabs and the grid
-    __shared__ __align__(16) float sCx[3][TX + 8];
-    __shared__ __align__(16) float sCy[3][TY + 8];
 
     const Geom &G = A.g;
     const int tid = threadIdx.x;
     const int tx = tid % (TX / 4), ty = tid / (TX / 4);
     const int tile = blockIdx.x;
     const int x0 = (tile % A.tiles_x) * TX, y0 = (tile / A.tiles_x) * TY;
-    const int z0 = A.zbase + blockIdx.y * A.zchunk;
-    const int z1 = min(A.zend, z0 + A.zchunk);
     const int shot = blockIdx.z;
     const int gx = x0 + 4 * tx, gy = y0 + ty;
     const int niter = z1 - z0 + 8;
@@ -326,12 +346,12 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
     for (int d = 0; d < 3; ++d)
         stape[d] = A.slab_tape[d] ? A.slab_tape[d] + (long long)shot * G.slab[d] * 4 : nullptr;
 
-    for (int i = tid; i < 3 * (TX + 8); i += NTHREADS) {
+    for (int i = tid; kEdge && i < 3 * (TX + 8); i += NTHREADS) {
         const int c = i / (TX + 8), x = x0 - 4 + i % (TX + 8);
         const bool in = x >= 0 && x < G.nx && in_slab(x, G.nx, G.lo[0], G.hi[0]);
         sCx[c][i % (TX + 8)] = in ? (c == 0 ? A.cb[0][x] : (c == 1 ? A.ca[0][x] : A.ck[0][x])) : (c == 2 ? 1.f : 0.f);
     }
-    for (int i = tid; i < 3 * (TY + 8); i += NTHREADS) {
+    for (int i = tid; kEdge && i < 3 * (TY + 8); i += NTHREADS) {
         const int c = i / (TY + 8), y = y0 - 4 + i % (TY + 8);
         const bool in = y >= 0 && y < G.ny && in_slab(y, G.ny, G.lo[1], G.hi[1]);
         sCy[c][i % (TY + 8)] = in ? (c == 0 ? A.cb[1][y] : (c == 1 ? A.ca[1][y] : A.ck[1][y])) : (c == 2 ? 1.f : 0.f);
@@ -344,12 +364,12 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
     for (int i = 0; i < 4; ++i)
         mk[i] = ((gx + i < G.nx) && (gy < G.ny)) ? 1.f : 0.f;
     const V4 mask = V4{make_float2(mk[0], mk[1]), make_float2(mk[2], mk[3])};
-    const bool full_tile = (x0 + TX <= G.nx) && (y0 + TY <= G.ny);
+    const bool full_tile = !kEdge || ((x0 + TX <= G.nx) && (y0 + TY <= G.ny));
     const long long rowofs = (long long)gy * G.nxp + gx;
 
     // which memory variables this thread touches (own vector, halo vector)
-    const bool own_x = G.w[0] > 0 && gy < G.ny && gx < G.nx && (gx < G.lo[0] || gx + 3 >= G.nx - G.hi[0]);
-    const bool own_y = G.w[1] > 0 && row_ok && in_slab(gy, G.ny, G.lo[1], G.hi[1]);
+    const bool own_x = kEdge && G.w[0] > 0 && gy < G.ny && gx < G.nx && (gx < G.lo[0] || gx + 3 >= G.nx - G.hi[0]);
+    const bool own_y = kEdge && G.w[1] > 0 && row_ok && in_slab(gy, G.ny, G.lo[1], G.hi[1]);
 
     // halo task of this thread: one pair of nodes.  Threads 0..127: the y
     // halo (8 rows x 16 pairs), threads 128..255: the x halo (32 rows x 2
@@ -363,8 +383,8 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
     const int xh_x = xh_k < 2 ? x0 - 4 + 2 * xh_k : x0 + TX + 2 * (xh_k - 2);
     const int xh_y = y0 + ((tid - 128) >> 2);
     const bool yh_in = yh_y >= 0 && yh_y < G.ny;
-    const bool halo_psi_y = do_yhalo && G.w[1] > 0 && yh_in && yh_x < G.nxp && in_slab(yh_y, G.ny, G.lo[1], G.hi[1]);
-    const bool halo_psi_x = !do_yhalo && G.w[0] > 0 && xh_y < G.ny && xh_x >= 0 && xh_x < G.nx &&
+    const bool halo_psi_y = kEdge && do_yhalo && G.w[1] > 0 && yh_in && yh_x < G.nxp && in_slab(yh_y, G.ny, G.lo[1], G.hi[1]);
+    const bool halo_psi_x = kEdge && !do_yhalo && G.w[0] > 0 && xh_y < G.ny && xh_x >= 0 && xh_x < G.nx &&
                             (xh_x < G.lo[0] || xh_x + 1 >= G.nx - G.hi[0]);
     const bool slab_thread = own_x || own_y || halo_psi_x || halo_psi_y;
 
@@ -455,12 +475,12 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
         const bool active = t >= z0;
         const unsigned char *S = smem + (it % NSTAGE) * L::BYTES;
 
-        const bool zs_v = row_ok && zv >= 0 && zv < G.nz && in_slab(zv, G.nz, G.lo[2], G.hi[2]);
-        const bool zs_p = active && row_ok && in_slab(t, G.nz, G.lo[2], G.hi[2]);
+        const bool zs_v = kEdge && row_ok && zv >= 0 && zv < G.nz && in_slab(zv, G.nz, G.lo[2], G.hi[2]);
+        const bool zs_p = kEdge && active && row_ok && in_slab(t, G.nz, G.lo[2], G.hi[2]);
 
         // L2 prefetch of the memory variables of the next plane, so that the
         // slab loads of the next iteration do not wait on HBM
-        if (FDTD_PREFETCH) {
+        if (FDTD_PREFETCH && kEdge) {
             const int tn = t + 1, zn = zv + 1;
             if (row_ok && zn < G.nz && zn >= 0 && in_slab(zn, G.nz, G.lo[2], G.hi[2]))
                 prefetch_l2(psiv_in[2] + slab_index(G, 2, zn, gy, gx));
@@ -580,8 +600,10 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
                           make_float2(sCy[2][r], sCy[2][r]));
                 }
                 float2 vn = fma2(ndtr, g, lds2<T>(S + L::OFF_VY, r * TX + (yh_x - x0)));
-                vn.x = (yh_in && yh_x < G.nx) ? vn.x : 0.f;
-                vn.y = (yh_in && yh_x + 1 < G.nx) ? vn.y : 0.f;
+                if (kEdge) {
+                    vn.x = (yh_in && yh_x < G.nx) ? vn.x : 0.f;
+                    vn.y = (yh_in && yh_x + 1 < G.nx) ? vn.y : 0.f;
+                }
                 *reinterpret_cast<float2 *>(svy + r * TX + (yh_x - x0)) = vn;
             } else {
                 const int lrow = (xh_y - y0 + 8) * L::PW, lx = xh_x - x0 + 8;
@@ -594,8 +616,10 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
                           *reinterpret_cast<const float2 *>(&sCx[1][cx]), *reinterpret_cast<const float2 *>(&sCx[2][cx]));
                 }
                 float2 vn = fma2(ndtr, g, lds2<T>(S + L::OFF_VX, (xh_y - y0) * L::VXW + lx));
-                vn.x = (xh_y < G.ny && xh_x >= 0 && xh_x < G.nx) ? vn.x : 0.f;
-                vn.y = (xh_y < G.ny && xh_x + 1 >= 0 && xh_x + 1 < G.nx) ? vn.y : 0.f;
+                if (kEdge) {
+                    vn.x = (xh_y < G.ny && xh_x >= 0 && xh_x < G.nx) ? vn.x : 0.f;
+                    vn.y = (xh_y < G.ny && xh_x + 1 >= 0 && xh_x + 1 < G.nx) ? vn.y : 0.f;
+                }
                 *reinterpret_cast<float2 *>(svx + (xh_y - y0) * L::SVXW + cx) = vn;
             }
         }
@@ -693,6 +717,30 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
 }
 
 template <typename T>
+__global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
+    fdtd_step_kernel(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mPq,
+                     const __grid_constant__ CUtensorMap mVX, const __grid_constant__ CUtensorMap mVY,
+                     const __grid_constant__ CUtensorMap mVZ, const __grid_constant__ CUtensorMap mK,
+                     const StepArgs A)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    // CPML coefficients (b, a, 1/kappa) of the tile's x range [x0-4, x0+TX+4)
+    // and y range [y0-4, y0+TY+4); 0, 0, 1 outside the slabs and the grid
+    __shared__ __align__(16) float sCx[3][TX + 8];
+    __shared__ __align__(16) float sCy[3][TY + 8];
+    const Geom &G = A.g;
+    const int x0 = (blockIdx.x % A.tiles_x) * TX, y0 = (blockIdx.x / A.tiles_x) * TY;
+    int z0, z1;
+    chunk_range(A, blockIdx.y, &z0, &z1);
+    const bool interior = x0 - 4 >= G.lo[0] && x0 + TX + 4 <= G.nx - G.hi[0] && y0 - 4 >= G.lo[1] &&
+                          y0 + TY + 4 <= G.ny - G.hi[1] && z0 - 4 >= G.lo[2] && z1 + 4 <= G.nz - G.hi[2];
+    if (interior)
+        step_body<T, false>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy);
+    else
+        step_body<T, true>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy);
+}
+
+template <typename T>
 static cudaError_t launch_step_t(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream)
 {
     using L = StageLayout<T>;
@@ -704,7 +752,7 @@ static cudaError_t launch_step_t(const fdtd_ctx *c, const StepArgs &a, int set, 
             return e;
         attr_done = true;
     }
-    dim3 grid(c->tiles_x * c->tiles_y, (a.zend - a.zbase + a.zchunk - 1) / a.zchunk, c->d.nshots);
+    dim3 grid(c->tiles_x * c->tiles_y, chunk_count(a), c->d.nshots);
     fdtd_step_kernel<T><<<grid, NTHREADS, L::SMEM, stream>>>(c->maps[set][0], c->maps[set][1], c->maps[set][2],
                                                               c->maps[set][3], c->maps[set][4], c->mapK, a);
     return cudaGetLastError();

@@ -215,3 +215,42 @@ def test_energy_and_misfit_reductions_fp64():
     assert abs(J - 0.5 * float(np.sum(r * r))) <= 1e-6 * max(J, 1e-30)
     assert np.allclose(resid.cpu().numpy()[:, :4], (traces - dobs).cpu().numpy()[:, :4])
     assert np.all(resid.cpu().numpy()[:, 4:] == 0)
+
+
+def test_interior_and_edge_chunkings_give_identical_state(monkeypatch):
+    """100 x 96 x 100, 24 shots: large enough that the default launch cuts z
+    into one chunk per CPML end plus interior chunks (whose interior tiles run
+    the kernel's interior form).  The state after 6 steps, with sources and
+    receivers, equals bit for bit the one of uniform 7-plane chunks, where
+    every CTA runs the general form."""
+    Fdtd = _fdtd()
+    shape, cells, nshots, n = (100, 96, 100), (4, 5, 4, 6, 5, 4), 24, 6
+    h, c = 10.0, 2500.0
+    dt = 0.5 * h / c
+    vel = synth.layered_model(shape, seed=4, vmin=1600.0, vmax=c, amp_cells=2.0)
+    src = synth.shot_positions(shape, cells, 9, nshots, z=cells[4] + 2)
+    wav = np.stack([synth.ricker(n, dt, 25.0) for _ in range(nshots)]).astype(np.float32)
+    rec = synth.receiver_grid(shape, cells, 4, 4, 50)
+    states = {s: synth.random_state(shape, cells, seed=70 + s, **state_scales(h, dt)) for s in (0, 11, 23)}
+    out = []
+    for zc in (None, "7"):
+        if zc is None:
+            monkeypatch.delenv("FDTD_ZCHUNK", raising=False)
+        else:
+            monkeypatch.setenv("FDTD_ZCHUNK", zc)
+        sim = Fdtd(shape, h, dt, nshots=nshots, cpml_cells=cells, nt_max=n, nrec_max=len(rec))
+        sim.set_model(torch.from_numpy(vel).cuda())
+        sim.set_cpml(R=1e-5, c_ref=c)
+        sim.inject(src, torch.from_numpy(wav).cuda())
+        tr = sim.record(rec)
+        for s, st in states.items():
+            set_gpu_state(sim, st, s)
+        sim.step(n)
+        sim.sync()
+        out.append(({s: {f: sim.get(f, s) for f in FIELDS} for s in states}, tr.clone()))
+        del sim
+    for s in states:
+        for f in FIELDS:
+            assert torch.equal(out[0][0][s][f], out[1][0][s][f]), (s, f)
+    assert torch.equal(out[0][1], out[1][1])
+    assert float(out[0][1].abs().max()) > 0
