@@ -153,7 +153,7 @@ void make_layout(const fdtd_desc *d, Layout *L)
     L->wav = take(S * d->nt_max * 4);
     L->src = take(S * 3 * 4);
     L->rec = take((size_t)std::max(d->nrec_max, 1) * 16);
-    L->rec_off = take((size_t)(L->tiles_x * L->tiles_y + 1) * 4);
+    L->rec_off = take(((size_t)L->tiles_x * L->tiles_y * g.nz + 1) * 4);
     L->err = take(16);
     L->red = take(8 * 1024);
     L->minmax = take(16);
@@ -744,7 +744,7 @@ int fdtd_create(const fdtd_desc *desc, void *workspace, size_t workspace_bytes, 
             coef[(d * 3 + 2) * nmax + i] = 1.f;
     cudaError_t e = cudaMemcpyAsync(c->coef, coef.data(), coef.size() * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(c->rec_off, 0, (size_t)(c->tiles_x * c->tiles_y + 1) * 4, c->stream);
+        e = cudaMemsetAsync(c->rec_off, 0, ((size_t)c->tiles_x * c->tiles_y * c->g.nz + 1) * 4, c->stream);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess || memset_state(c) != FDTD_OK) {
@@ -906,17 +906,20 @@ int fdtd_record(fdtd_ctx *c, const int *rec_zyx, int nrec, float *traces)
             return rv[a].y < rv[b].y;
         return rv[a].z < rv[b].z;
     });
+    // ranges per (tile, plane): the kernel reads a plane's receivers together
+    const int nz = c->g.nz;
+    const size_t nbin = (size_t)ntiles * nz;
     std::vector<int4> sorted(std::max(nrec, 1));
-    std::vector<int> off(ntiles + 1, 0);
+    std::vector<int> off(nbin + 1, 0);
     for (int i = 0; i < nrec; ++i) {
         sorted[i] = rv[order[i]];
-        off[tile_of[order[i]] + 1]++;
+        off[(size_t)tile_of[order[i]] * nz + sorted[i].x + 1]++;
     }
-    for (int t = 0; t < ntiles; ++t)
-        off[t + 1] += off[t];
+    for (size_t b = 0; b < nbin; ++b)
+        off[b + 1] += off[b];
     if (nrec > 0)
         CUDA_TRY(c, cudaMemcpyAsync(c->rec, sorted.data(), sizeof(int4) * nrec, cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c->rec_off, off.data(), sizeof(int) * (ntiles + 1), cudaMemcpyHostToDevice,
+    CUDA_TRY(c, cudaMemcpyAsync(c->rec_off, off.data(), sizeof(int) * (nbin + 1), cudaMemcpyHostToDevice,
                                 c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->nrec = nrec;

@@ -353,8 +353,8 @@ struct StepArgs {
     const int *src;                 // [nshots][3] (z, y, x)
     const float *wavelet;           // [nshots][nt_w]
     int nt_w;
-    const int *rec_off;             // [tiles + 1]
-    const int4 *rec;                // (z, y, x, r) sorted by tile, z
+    const int *rec_off;             // [tiles * nz + 1]: receivers of (tile, plane z) are rec[off .. next off)
+    const int4 *rec;                // (z, y, x, r) sorted by tile, z, y, x
     int nrec, nt_max;
     float *traces;                  // [nshots][nt_max][nrec] or null
     float *s_tape;                  // [nshots][vol] pressure bracket of this step, or null

@@ -394,12 +394,9 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
     const float wsrc = (A.src && A.t < A.nt_w) ? A.sscale * A.wavelet[(long long)shot * A.nt_w + A.t] : 0.f;
     const bool src_here = A.src && sy == gy && sx >= gx && sx < gx + 4 && sz >= z0 && sz < z1;
     // receivers of this tile (sorted by z)
-    int rc = 0, r1 = 0;
+    // receivers of this tile: rec_off[tile * nz + z] .. [+ 1] are those on plane z
     const bool rec_on = A.traces != nullptr && A.nrec > 0 && A.t < A.nt_max;
-    if (rec_on) {
-        rc = A.rec_off[tile];
-        r1 = A.rec_off[tile + 1];
-    }
+    const int *roff = A.rec_off + (long long)tile * G.nz;
 
     if (tid == 0) {
         prefetch_tmap(&mP);
@@ -692,17 +689,18 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     stsf(A.s_tape + fofs + o, sb);
             }
             if (rec_on) {
-                while (rc < r1 && A.rec[rc].x < t)
-                    ++rc;
-                for (int r = rc; r < r1; ++r) {
-                    const int4 q = A.rec[r];
-                    if (q.x != t)
-                        break;
-                    if (q.y == gy && q.z >= gx && q.z < gx + 4) {
-                        const int i = q.z - gx;
-                        const float v = i == 0 ? pn.a.x : (i == 1 ? pn.a.y : (i == 2 ? pn.b.x : pn.b.y));
+                const int r0 = __ldg(roff + t), r1 = __ldg(roff + t + 1);
+                if (r0 < r1) {
+                    // the plane's new p goes to this stage's K slots, which each
+                    // thread has just read for its own nodes; then the CTA reads
+                    // the plane's receivers together
+                    float *pl = reinterpret_cast<float *>(smem + (it % NSTAGE) * L::BYTES + L::OFF_K);
+                    stsf(pl + ty * TX + 4 * tx, pn);
+                    __syncthreads();
+                    for (int r = r0 + tid; r < r1; r += NTHREADS) {
+                        const int4 q = A.rec[r];
                         // read back through the storage type so traces equal the stored state
-                        T tmp = T(v);
+                        T tmp = T(pl[(q.y - y0) * TX + (q.z - x0)]);
                         A.traces[((long long)shot * A.nt_max + A.t) * A.nrec + q.w] = A.inv_sscale * Io<T>::ld1(&tmp);
                     }
                 }
