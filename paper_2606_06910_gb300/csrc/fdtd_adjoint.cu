@@ -10,6 +10,10 @@
 //   stage B (velocity):  r = -dtr lam_v_d ; lam_g_d = kinv r + a (lam_psiv_d + r)
 //                        lam_p -= sum_d D_d lam_g_d ; lam_psiv_d <- b (lam_psiv_d + r)
 // and dJ/dK += -(dt / vscale) S lam_p with S the taped pressure bracket.
+// (Here kdt holds the coefficient with its sign, -dt K / vscale, so q = kdt
+// lam_p.)  The library stores the adjoint pressure as mu = kdt lam_p, the
+// quantity stage A differentiates: q = mu, stage B updates mu -= kdt sum D
+// lam_g, and dJ/dK uses lam_p = mu / kdt.
 #include "fdtd_internal.cuh"
 
 namespace fdtd {
@@ -45,7 +49,7 @@ __device__ __forceinline__ float lam_h(const AdjArgs &A, int d, int z, int y, in
     if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz)
         return 0.f;
     const long long o = (long long)z * g.plane + (long long)y * g.nxp + x;
-    const float q = A.kdt[o] * ap[o];   // kdt holds -dt K / vscale
+    const float q = ap[o];   // mu = kdt lam_p
     const int k = axis_coord(d, z, y, x);
     if (in_slab(k, axis_len(g, d), g.lo[d], g.hi[d]))
         return A.ck[d][k] * q + A.ca[d][k] * (apsip_in[slab_index(g, d, z, y, x)] + q);
@@ -77,9 +81,8 @@ __global__ void adj_stage_a_kernel(AdjArgs A)
     const long long fo = (long long)shot * g.vol;
     const long long o = (long long)z * g.plane + (long long)y * g.nxp + x;
     const float *ap = A.ap + fo;
-    const float lp = ap[o];
-    A.gradK[fo + o] += -A.dt_over_vs * A.s_tape[fo + o] * lp;
-    const float q = A.kdt[o] * lp;
+    const float q = ap[o];   // mu = kdt lam_p
+    A.gradK[fo + o] += -A.dt_over_vs * A.s_tape[fo + o] * (q / A.kdt[o]);
     const int dz[3] = {0, 0, 1}, dy[3] = {0, 1, 0}, dx[3] = {1, 0, 0};
     for (int d = 0; d < 3; ++d) {
         const float *psin = A.apsip_in[d] + (long long)shot * g.slab[d];
@@ -137,11 +140,11 @@ __global__ void adj_stage_b_kernel(AdjArgs A)
             }
         }
     }
-    A.ap[fo + o] -= acc;
+    A.ap[fo + o] -= A.kdt[o] * acc;
 }
 
-__global__ void adj_inject_kernel(float *ap, Geom g, const int4 *rec, int nrec, int nshots, const float *resid,
-                                  int nt_max, int n)
+__global__ void adj_inject_kernel(float *ap, const float *kdt, Geom g, const int4 *rec, int nrec, int nshots,
+                                  const float *resid, int nt_max, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrec * nshots)
@@ -149,7 +152,8 @@ __global__ void adj_inject_kernel(float *ap, Geom g, const int4 *rec, int nrec, 
     const int shot = i / nrec, k = i % nrec;
     const int4 q = rec[k];
     const float r = resid[((long long)shot * nt_max + n) * nrec + q.w];
-    atomicAdd(&ap[(long long)shot * g.vol + (long long)q.x * g.plane + (long long)q.y * g.nxp + q.z], r);
+    const long long o = (long long)q.x * g.plane + (long long)q.y * g.nxp + q.z;
+    atomicAdd(&ap[(long long)shot * g.vol + o], kdt[o] * r);   // mu = kdt lam_p
 }
 
 __global__ void grad_vel_kernel(const float *gradK, const float *kdt, Geom g, int nshots, double vs_over_dt,
@@ -187,8 +191,8 @@ cudaError_t launch_adj_inject(const fdtd_ctx *c, const float *resid, int n)
     const int tot = c->nrec * c->d.nshots;
     if (tot == 0)
         return cudaSuccess;
-    adj_inject_kernel<<<(tot + 255) / 256, 256, 0, c->stream>>>(c->ap, c->g, c->rec, c->nrec, c->d.nshots, resid,
-                                                                c->d.nt_max, n);
+    adj_inject_kernel<<<(tot + 255) / 256, 256, 0, c->stream>>>(c->ap, c->kdt, c->g, c->rec, c->nrec, c->d.nshots,
+                                                                resid, c->d.nt_max, n);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ cudaError_t launch_step(const fdtd_ctx *c, const StepArgs &a, int set, cudaStrea
 int step_occupancy(int storage, int *blocks);
 cudaError_t launch_model(fdtd_ctx *c, const float *vel);
 cudaError_t launch_field(const fdtd_ctx *c, bool get, void *internal, float *dense, int kind, float scale,
-                         bool is_f32);
+                         bool is_f32, const float *kscale);
 cudaError_t launch_energy(const fdtd_ctx *c, const void *p, const int *box);
 cudaError_t launch_misfit(const fdtd_ctx *c, const float *dobs, int nt, float *resid);
 cudaError_t launch_ska_to_coef(const fdtd_ctx *c, const float *ska, int L);
@@ -32,7 +32,7 @@ cudaError_t launch_adam(float *th, const float *g, float *m, float *v, int n, fl
 cudaError_t launch_adj_inject(const fdtd_ctx *c, const float *resid, int n);
 cudaError_t launch_grad_vel(const fdtd_ctx *c, float *grad_vel);
 cudaError_t adjoint_step(fdtd_ctx *c, const float *s_tape, float *const slab_tape[3], bool want_prof);
-cudaError_t adjoint_step_tiled(fdtd_ctx *c, const float *s_tape);
+cudaError_t adjoint_step_fused(fdtd_ctx *c, const float *s_tape);
 int mlp_nparam();
 int mlp_bwd_max();
 }  // namespace fdtd
@@ -68,7 +68,7 @@ struct Layout {
     size_t p[2], v[3][2], psiv[3][2], psip[3];
     size_t kdt, coef, wav, src, rec, rec_off, err, red, minmax;
     int ncp;
-    size_t ckpt, ckpt_slot, tape_s, tape_slab[3], ap, av[3], apsiv[3][2], apsip[3][2], gradK, gprof;
+    size_t ckpt, ckpt_slot, tape_s, tape_slab[3], ap[2], av[3][2], apsiv[3][2], apsip[3][2], gradK, gprof;
     size_t total;
 };
 
@@ -169,9 +169,11 @@ void make_layout(const fdtd_desc *d, Layout *L)
         L->tape_s = take((size_t)C * S * g.vol * 4);
         for (int a = 0; a < 3; ++a)
             L->tape_slab[a] = d->cpml_grad ? take((size_t)C * S * g.slab[a] * 16) : 0;
-        L->ap = take(S * g.vol * 4);
-        for (int a = 0; a < 3; ++a)
-            L->av[a] = take(S * g.vol * 4);
+        for (int s = 0; s < 2; ++s) {
+            L->ap[s] = take(S * g.vol * 4);
+            for (int a = 0; a < 3; ++a)
+                L->av[a][s] = take(S * g.vol * 4);
+        }
         for (int a = 0; a < 3; ++a)
             for (int s = 0; s < 2; ++s) {
                 L->apsiv[a][s] = take(S * g.slab[a] * 4);
@@ -242,13 +244,14 @@ int build_maps(fdtd_ctx *c)
     if (st || c->ncp == 0)
         return st;
     const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const uint32_t b40[4] = {TX + 8, TY + 8, 1, 1}, bx[4] = {TX + 8, TY, 1, 1}, by[4] = {TX, TY + 8, 1, 1};
-    if ((st = make_map(c, &c->amaps[0], c->ap, 4, f32, 4, b40)) || (st = make_map(c, &c->amaps[1], c->ap, 4, f32, 4, bQ)) ||
-        (st = make_map(c, &c->amaps[2], c->kdt, 3, f32, 4, b40)) ||
-        (st = make_map(c, &c->amaps[3], c->av[0], 4, f32, 4, bx)) ||
-        (st = make_map(c, &c->amaps[4], c->av[1], 4, f32, 4, by)) ||
-        (st = make_map(c, &c->amaps[5], c->av[2], 4, f32, 4, bQ)))
-        return st;
+    const uint32_t b48[4] = {TX + 16, TY + 16, 1, 1}, bx[4] = {TX + 8, TY, 1, 1}, by[4] = {TX, TY + 8, 1, 1};
+    for (int s = 0; s < 2; ++s)
+        if ((st = make_map(c, &c->amaps[s][0], c->apb[s], 4, f32, 4, b48)) ||
+            (st = make_map(c, &c->amaps[s][1], c->apb[s], 4, f32, 4, bQ)) ||
+            (st = make_map(c, &c->amaps[s][2], c->avb[0][s], 4, f32, 4, bx)) ||
+            (st = make_map(c, &c->amaps[s][3], c->avb[1][s], 4, f32, 4, by)) ||
+            (st = make_map(c, &c->amaps[s][4], c->avb[2][s], 4, f32, 4, bQ)))
+            return st;
     return FDTD_OK;
 }
 
@@ -589,9 +592,14 @@ int memset_state(fdtd_ctx *c)
             CUDA_TRY(c, cudaMemsetAsync(c->psip[d], 0, slab_bytes(c, d), c->stream));
     if (c->ncp > 0) {
         const size_t fb = (size_t)c->d.nshots * c->g.vol * 4;
-        CUDA_TRY(c, cudaMemsetAsync(c->ap, 0, fb, c->stream));
+        c->aset = 0;
+        c->ap = c->apb[0];
+        for (int s = 0; s < 2; ++s)
+            CUDA_TRY(c, cudaMemsetAsync(c->apb[s], 0, fb, c->stream));
         for (int d = 0; d < 3; ++d) {
-            CUDA_TRY(c, cudaMemsetAsync(c->av[d], 0, fb, c->stream));
+            c->av[d] = c->avb[d][0];
+            for (int s = 0; s < 2; ++s)
+                CUDA_TRY(c, cudaMemsetAsync(c->avb[d][s], 0, fb, c->stream));
             const size_t sb = (size_t)c->d.nshots * c->g.slab[d] * 4;
             for (int s = 0; s < 2; ++s)
                 if (sb) {
@@ -720,13 +728,18 @@ int fdtd_create(const fdtd_desc *desc, void *workspace, size_t workspace_bytes, 
         c->tape_s = (float *)(w + L.tape_s);
         for (int d = 0; d < 3; ++d) {
             c->tape_slab[d] = desc->cpml_grad ? (float *)(w + L.tape_slab[d]) : nullptr;
-            c->av[d] = (float *)(w + L.av[d]);
+            for (int s = 0; s < 2; ++s)
+                c->avb[d][s] = (float *)(w + L.av[d][s]);
+            c->av[d] = c->avb[d][0];
             for (int s = 0; s < 2; ++s) {
                 c->apsiv[d][s] = (float *)(w + L.apsiv[d][s]);
                 c->apsip[d][s] = (float *)(w + L.apsip[d][s]);
             }
         }
-        c->ap = (float *)(w + L.ap);
+        for (int s = 0; s < 2; ++s)
+            c->apb[s] = (float *)(w + L.ap[s]);
+        c->ap = c->apb[0];
+        c->aset = 0;
         c->gradK = (float *)(w + L.gradK);
         c->gprof = (float *)(w + L.gprof);
     }
@@ -987,9 +1000,8 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
     if (grad_cpml && !c->d.cpml_grad)
         return fail(c, FDTD_EINVAL, "grad_cpml needs cpml_grad at create time");
     const bool want_prof = grad_cpml != nullptr;
-    const size_t fb4 = (size_t)c->d.nshots * c->g.vol * 4;
     const int nmax = nmax_of(c->g);
-    CUDA_TRY(c, cudaMemsetAsync(c->gradK, 0, fb4, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->gradK, 0, (size_t)c->d.nshots * c->g.vol * 4, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->gprof, 0, (size_t)9 * nmax * 4, c->stream));
     const int tend = c->t;
     for (int seg = (tend - 1) / C; seg >= 0 && tend > 0; --seg) {
@@ -1017,11 +1029,11 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
                 slab[d] = c->tape_slab[d] ? c->tape_slab[d] + (size_t)(k - s0) * c->d.nshots * c->g.slab[d] * 4
                                           : nullptr;
             const float *sk = c->tape_s + (size_t)(k - s0) * c->d.nshots * c->g.vol;
-            // the tiled kernels carry no profile gradient; that path keeps the node-per-thread kernels
+            // the fused kernel carries no profile gradient; that path keeps the node-per-thread kernels
             if (want_prof)
                 CUDA_TRY(c, adjoint_step(c, sk, slab, true));
             else
-                CUDA_TRY(c, adjoint_step_tiled(c, sk));
+                CUDA_TRY(c, adjoint_step_fused(c, sk));
         }
     }
     if (grad_vel)
@@ -1093,7 +1105,7 @@ int fdtd_get_field(fdtd_ctx *c, int which, int shot, float *dst)
         CUDA_TRY(c, cudaMemsetAsync(dst, 0, (size_t)c->g.nz * c->g.ny * c->g.nx * 4, c->stream));
         return FDTD_OK;
     }
-    CUDA_TRY(c, launch_field(c, true, ptr, dst, kind, scale, f32));
+    CUDA_TRY(c, launch_field(c, true, ptr, dst, kind, scale, f32, which == FDTD_ADJ_P ? c->kdt : nullptr));
     return FDTD_OK;
 }
 
@@ -1147,7 +1159,8 @@ int fdtd_set_field(fdtd_ctx *c, int which, int shot, const float *src)
         scale *= c->sscale;
     if (kind > 0 && c->g.slab[kind - 1] == 0)
         return FDTD_OK;
-    CUDA_TRY(c, launch_field(c, false, ptr, const_cast<float *>(src), kind, scale, f32));
+    CUDA_TRY(c, launch_field(c, false, ptr, const_cast<float *>(src), kind, scale, f32,
+                             which == FDTD_ADJ_P ? c->kdt : nullptr));
     return FDTD_OK;
 }
 

@@ -54,7 +54,8 @@ cudaError_t launch_model(fdtd_ctx *c, const float *vel)
 // kind-1.  Dense side: float [nz][ny][nx].
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void get_field_kernel(const T *__restrict__ src, float *__restrict__ dst, Geom g, int kind, float scale)
+__global__ void get_field_kernel(const T *__restrict__ src, float *__restrict__ dst, Geom g, int kind, float scale,
+                                 const float *__restrict__ div)
 {
     const long long n = (long long)g.nz * g.ny * g.nx;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -64,7 +65,10 @@ __global__ void get_field_kernel(const T *__restrict__ src, float *__restrict__ 
         const int z = (int)(i / ((long long)g.nx * g.ny));
         float v = 0.f;
         if (kind == 0) {
-            v = Io<T>::ld1(src + (long long)z * g.plane + (long long)y * g.nxp + x);
+            const long long o = (long long)z * g.plane + (long long)y * g.nxp + x;
+            v = Io<T>::ld1(src + o);
+            if (div)
+                v /= div[o];
         } else {
             const int d = kind - 1;
             const int q = d == 0 ? x : (d == 1 ? y : z);
@@ -77,7 +81,8 @@ __global__ void get_field_kernel(const T *__restrict__ src, float *__restrict__ 
 }
 
 template <typename T>
-__global__ void set_field_kernel(T *__restrict__ dstf, const float *__restrict__ src, Geom g, int kind, float scale)
+__global__ void set_field_kernel(T *__restrict__ dstf, const float *__restrict__ src, Geom g, int kind, float scale,
+                                 const float *__restrict__ mul)
 {
     const long long n = (long long)g.nz * g.ny * g.nx;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -86,7 +91,8 @@ __global__ void set_field_kernel(T *__restrict__ dstf, const float *__restrict__
         const int y = (int)((i / g.nx) % g.ny);
         const int z = (int)(i / ((long long)g.nx * g.ny));
         if (kind == 0) {
-            Io<T>::st1(dstf + (long long)z * g.plane + (long long)y * g.nxp + x, src[i] * scale);
+            const long long o = (long long)z * g.plane + (long long)y * g.nxp + x;
+            Io<T>::st1(dstf + o, mul ? src[i] * scale * mul[o] : src[i] * scale);
         } else {
             const int d = kind - 1;
             const int q = d == 0 ? x : (d == 1 ? y : z);
@@ -97,29 +103,33 @@ __global__ void set_field_kernel(T *__restrict__ dstf, const float *__restrict__
     }
 }
 
+// `kscale` (or NULL): per-node factor of a full field, divided out on get and
+// multiplied in on set (the adjoint pressure is stored as kdt lam_p)
 cudaError_t launch_field(const fdtd_ctx *c, bool get, void *internal, float *dense, int kind, float scale,
-                         bool is_f32)
+                         bool is_f32, const float *kscale)
 {
     const int blocks = 1216, threads = 256;
     if (is_f32 || c->d.storage == FDTD_F32) {
         if (get)
             get_field_kernel<float><<<blocks, threads, 0, c->stream>>>((const float *)internal, dense, c->g, kind,
-                                                                        scale);
+                                                                        scale, kscale);
         else
-            set_field_kernel<float><<<blocks, threads, 0, c->stream>>>((float *)internal, dense, c->g, kind, scale);
+            set_field_kernel<float><<<blocks, threads, 0, c->stream>>>((float *)internal, dense, c->g, kind, scale,
+                                                                        kscale);
     } else if (c->d.storage == FDTD_F16) {
         if (get)
             get_field_kernel<__half><<<blocks, threads, 0, c->stream>>>((const __half *)internal, dense, c->g, kind,
-                                                                         scale);
+                                                                         scale, nullptr);
         else
-            set_field_kernel<__half><<<blocks, threads, 0, c->stream>>>((__half *)internal, dense, c->g, kind, scale);
+            set_field_kernel<__half><<<blocks, threads, 0, c->stream>>>((__half *)internal, dense, c->g, kind, scale,
+                                                                         nullptr);
     } else {
         if (get)
             get_field_kernel<__nv_bfloat16><<<blocks, threads, 0, c->stream>>>((const __nv_bfloat16 *)internal,
-                                                                                dense, c->g, kind, scale);
+                                                                                dense, c->g, kind, scale, nullptr);
         else
             set_field_kernel<__nv_bfloat16><<<blocks, threads, 0, c->stream>>>((__nv_bfloat16 *)internal, dense,
-                                                                                c->g, kind, scale);
+                                                                                c->g, kind, scale, nullptr);
     }
     return cudaGetLastError();
 }

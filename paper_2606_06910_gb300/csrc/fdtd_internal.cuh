@@ -401,16 +401,18 @@ struct fdtd_ctx {
     size_t ckpt_slot_bytes;
     float *tape_s;          // [C][nshots][vol]
     float *tape_slab[3];    // [C][nshots][slab d][4]
-    float *ap, *av[3];      // adjoint p, v (FP32)
+    float *ap, *av[3];      // adjoint mu = kdt lam_p and lam_v (FP32): the current set of apb / avb
+    float *apb[2], *avb[3][2];
+    int aset;
     float *apsiv[3][2], *apsip[3][2];
     int acur;
     float *gradK;           // [nshots][vol]
     float *gprof;           // [3][3][nmax]
     CUtensorMap maps[2][5]; // per ping-pong set: P halo, P queue, VX, VY, VZ
     CUtensorMap mapK;
-    // adjoint (FP32, built when checkpoint slots exist): lam_p 40x40 and
-    // 32x32, kdt 40x40, lam_v_x 40x32, lam_v_y 32x40, lam_v_z 32x32
-    CUtensorMap amaps[6];
+    // adjoint (FP32, built when checkpoint slots exist), per set of mu /
+    // lam_v: mu 48x48 and 32x32, lam_v_x 40x32, lam_v_y 32x40, lam_v_z 32x32
+    CUtensorMap amaps[2][5];
     // temporal blocking (tblock_k > 1): one stream per step of a block, one
     // event per (step, z band); band b covers [b * tb_band, (b + 1) * tb_band)
     // and the last band runs to nz

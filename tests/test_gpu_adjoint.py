@@ -189,16 +189,22 @@ def test_autograd_function_matches_direct_adjoint():
     assert np.allclose(vel.grad.cpu().numpy(), g, rtol=1e-5, atol=1e-6 * np.max(np.abs(g)))
 
 
-@pytest.mark.parametrize("zchunk", [None, 8])
-def test_adjoint_state_matches_oracle_multi_tile(monkeypatch, zchunk):
+@pytest.mark.parametrize("shape,cells,zchunk", [
+    ((37, 70, 75), (5, 6, 4, 7, 3, 5), None),
+    ((37, 70, 75), (5, 6, 4, 7, 3, 5), 8),
+    ((60, 100, 100), (4, 4, 5, 3, 4, 4), 16),
+])
+def test_adjoint_state_matches_oracle_multi_tile(monkeypatch, shape, cells, zchunk):
     """Adjoint state and dJ/dc after 5 steps against the oracle's transpose,
-    field by field, on a grid of 3 x 3 tiles with ragged x and y tails, six
-    unequal layers and two shots; with the z range split into chunks of 8
-    (ragged last chunk) and with the default chunking."""
+    field by field, on grids of 3 x 3 and 4 x 4 tiles with ragged x and y
+    tails, six unequal layers and two shots; z in chunks of 8 (ragged last
+    chunk), of 16, or the default chunking.  On the 100 x 100 plane with
+    16-plane chunks some CTAs lie 8 nodes clear of every slab and edge and
+    run the kernel's interior form."""
     if zchunk is not None:
         monkeypatch.setenv("FDTD_ZCHUNK", str(zchunk))
     Fdtd = _Fdtd()
-    shape, cells, h, c = (37, 70, 75), (5, 6, 4, 7, 3, 5), 10.0, 2500.0
+    h, c = 10.0, 2500.0
     dt = 0.5 * h / c
     n, C, nshots = 5, 3, 2
     rng = np.random.default_rng(21)
