@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--cells", type=int, default=None, help="override CPML cells per face (0: no CPML)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--forms-only", action="store_true", help="measure only the forms (profiling runs)")
     ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock",
                     help="comma list of forms measured after the main line ('' for none)")
     return ap.parse_args()
@@ -336,20 +337,24 @@ def form_tblock(dev, nsteps=96, warm=8):
     return {"workload": f"layered512, {warm} + {nsteps} timed steps, z bands of 48 planes", "unit": UNIT, **out}
 
 
-def form_adjoint(dev, nt=800):
+def form_adjoint(dev, nt=800, nshots=None, every=None):
     """Forward with checkpoints + discrete adjoint, 256^3 x 16 shots, 128x128
-    receivers, checkpoint every 50 steps (gradient of the L2 misfit)."""
+    receivers, checkpoint every 50 steps (gradient of the L2 misfit).  The form
+    spec "adjoint:S:N" runs S shots over N steps with a checkpoint every N
+    (the small case the profiles use)."""
     import torch
     from paper_2606_06910_gb300 import synth
     from paper_2606_06910_gb300.fdtd import Fdtd
     w = synth.preset("adjoint256")
     rec = synth.receiver_grid(w.shape, w.cpml_cells, *w.extra["receivers"], z=w.cpml_cells[4])
     c0 = synth.gaussian_smooth(w.velocity(), w.extra["smooth_sigma"])
-    sim = Fdtd(w.shape, w.h, w.dt, nshots=w.nshots, cpml_cells=w.cpml_cells, nt_max=nt, nrec_max=len(rec),
-               checkpoint_every=w.extra["checkpoint_every"], device=dev)
+    ns = w.nshots if nshots is None else nshots
+    every = w.extra["checkpoint_every"] if every is None else every
+    sim = Fdtd(w.shape, w.h, w.dt, nshots=ns, cpml_cells=w.cpml_cells, nt_max=nt, nrec_max=len(rec),
+               checkpoint_every=every, device=dev)
     sim.set_model(torch.from_numpy(c0).to(dev))
     sim.set_cpml(R=w.R, c_ref=w.vmax)
-    sim.inject(w.sources(), torch.from_numpy(w.wavelet(nt)).to(dev))
+    sim.inject(w.sources()[:ns], torch.from_numpy(w.wavelet(nt)[:ns]).to(dev))
     sim.record(rec)
     dobs = torch.zeros_like(sim.traces)
     grad = torch.zeros(w.shape, device=dev)
@@ -359,10 +364,10 @@ def form_adjoint(dev, nt=800):
     t_adj = _timed(sim.stream, lambda: sim.adjoint(nt, resid, grad))
     sim.sync()
     ok = bool(torch.isfinite(grad).all()) and float(grad.abs().max()) > 0
-    pts = float(np.prod(w.shape)) * w.nshots * nt
+    pts = float(np.prod(w.shape)) * ns * nt
     del sim
     torch.cuda.empty_cache()
-    return {"workload": f"adjoint256: 256^3 x {w.nshots} shots x {nt} steps, C=50", "value": round(pts / (t_fwd + t_adj) / 1e6, 1),
+    return {"workload": f"adjoint256: 256^3 x {ns} shots x {nt} steps, C={every}", "value": round(pts / (t_fwd + t_adj) / 1e6, 1),
             "unit": UNIT + " (forward + adjoint)", "forward_s": round(t_fwd, 3), "adjoint_s": round(t_adj, 3),
             "misfit": J, "gradient_finite_nonzero": ok}
 
@@ -517,7 +522,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    out = run_ours(args, rank, world, local)
+    out = {} if args.forms_only else run_ours(args, rank, world, local)
     if rank == 0 and world == 1 and args.forms:
         import torch
         dev = torch.device("cuda", local)
@@ -529,6 +534,9 @@ def main():
                     forms[f] = form_storage(f, dev)
                 elif f == "adjoint":
                     forms[f] = form_adjoint(dev)
+                elif f.startswith("adjoint:"):
+                    _, ns, nt = f.split(":")
+                    forms[f] = form_adjoint(dev, nt=int(nt), nshots=int(ns), every=int(nt))
                 elif f == "learned":
                     forms[f] = form_learned(dev)
                 elif f == "tblock":
@@ -536,6 +544,10 @@ def main():
             except Exception as e:  # report, keep the main line
                 forms[f] = {"error": f"{type(e).__name__}: {e}"[:300]}
         out["forms"] = forms
+    if args.forms_only:
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
     if rank == 0:
         if not args.no_cpu_baseline:
             import oracle
