@@ -60,6 +60,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time (every rank gets it); `dist` is None on one rank."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, npts: float, nt: int, steps: int, total_ms: float) -> float:
+    """Mpoints/s of the whole job: every rank advances its own replica of the
+    grid (weak scaling), all in the slowest rank's time."""
+    return world * npts * nt * steps / (total_ms * 1e-3) / 1e6
+
+
 # ----------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ----------------------------------------------------------------------------
@@ -207,12 +223,9 @@ def run_ours(args, rank, world, local):
     sim.sync()
     total_ms = t0.elapsed_time(t1)
     kernel_ms = sum(a.elapsed_time(b) for a, b in kev)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     npts = float(np.prod(shape))
-    value = world * npts * nt * args.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_value(world, npts, nt, args.steps, total_ms)
 
     # roofline of the step kernel (the only kernel of sim.step)
     es = 4 if args.storage == "f32" else 2

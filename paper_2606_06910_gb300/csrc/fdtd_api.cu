@@ -284,11 +284,13 @@ void choose_zchunk(fdtd_ctx *c)
             best = zc;
         }
     }
-    // Large grids: chunks of about 48 planes (FP32) or 96 (16-bit storage).
+    // Large grids: chunks of about 32 planes (FP32) or 96 (16-bit storage).
     // CTAs that start together on short chunks stay close in z, so the halo
     // planes that neighbouring tiles read are still in L2; measured on
     // 256^3 x 16 shots, 512^3 and 1024^3 this beats the wave count above.
-    const int target = c->d.storage == FDTD_F32 ? 48 : 96;
+    int target = c->d.storage == FDTD_F32 ? 32 : 96;
+    if (const char *e = getenv("FDTD_ZTARGET"))   // tuning: planes per middle chunk
+        target = std::max(8, atoi(e));
     const int kt = (nz + target - 1) / target;
     const bool large = per_z * kt >= 2 * slots;
     if (large)
