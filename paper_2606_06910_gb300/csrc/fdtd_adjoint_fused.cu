@@ -328,6 +328,42 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
             prefetch_l2(A.s_tape + on);
             prefetch_l2(A.gradK + on);
         }
+        // memory variables of the next plane into L2 (CTAs that meet a slab)
+        if (kEdge && t + 1 >= z0 && t + 1 < z1) {
+            const int tn = t + 1;
+            if (xs_tile || ys_tile) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int v = tid + j * NTHREADS;
+                    if (v < TY * AW / 4) {
+                        const int r = v / (AW / 4), c = 4 * (v % (AW / 4)), x = x0 - AH + c, y = y0 + r;
+                        if (xs_tile && x >= 0 && x < G.nx && y < G.ny && (x < G.lo[0] || x + 3 >= G.nx - G.hi[0]))
+                            prefetch_l2(pspin[0] + slab_index(G, 0, tn, y, x));
+                    } else {
+                        const int u = v - TY * AW / 4, r = u / (TX / 4), c = 4 * (u % (TX / 4));
+                        const int y = y0 - AH + r, x = x0 + c;
+                        if (ys_tile && y >= 0 && y < G.ny && x < G.nxp && in_slab(y, G.ny, G.lo[1], G.hi[1]))
+                            prefetch_l2(pspin[1] + slab_index(G, 1, tn, y, x));
+                    }
+                }
+            }
+            if (own_x)
+                prefetch_l2(psvin[0] + slab_index(G, 0, tn, gy, gx));
+            if (own_y)
+                prefetch_l2(psvin[1] + slab_index(G, 1, tn, gy, gx));
+            if (do_yhalo && ys_tile && yh_in && yh_x < G.nxp && in_slab(yh_y, G.ny, G.lo[1], G.hi[1]))
+                prefetch_l2(psvin[1] + slab_index(G, 1, tn, yh_y, yh_x));
+            if (!do_yhalo && xs_tile && xh_in && xh_x >= 0 && xh_x < G.nx &&
+                (xh_x < G.lo[0] || xh_x + 1 >= G.nx - G.hi[0]))
+                prefetch_l2(psvin[0] + slab_index(G, 0, tn, xh_y, xh_x));
+        }
+        if (kEdge && row_ok) {
+            const int zq = t + 9, zv = t + 5;
+            if (zq < G.nz && in_slab(zq, G.nz, G.lo[2], G.hi[2]))
+                prefetch_l2(pspin[2] + slab_index(G, 2, zq, gy, gx));
+            if (zv >= 0 && zv < G.nz && in_slab(zv, G.nz, G.lo[2], G.hi[2]))
+                prefetch_l2(psvin[2] + slab_index(G, 2, zv, gy, gx));
+        }
         const bool ok = mbar_wait_bounded(&bar[it % ANS], (it / ANS) & 1, WAIT_LIMIT);
 
         // ---- z block: lam_h_z at t + 8, lam_v'_z and lam_g_z at t + 4, D_z lam_g_z at t
@@ -389,19 +425,23 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
         const F4 hz = dq(gq, w);
 
         // sources of D_x lam_h_x (row r <-> y0 + r, column c <-> x0 - 8 + c)
-        // and D_y lam_h_y (row r <-> y0 - 8 + r, column c <-> x0 + c)
-        const float *hxs = kEdge ? HX : S + L::P + AH * AW;
-        const float *hys = kEdge ? HY : S + L::P + AH;
+        // and D_y lam_h_y (row r <-> y0 - 8 + r, column c <-> x0 + c): shared
+        // memory where the tile meets an x (y) slab, else the staged mu plane
+        const float *hxs = xs_tile ? HX : S + L::P + AH * AW;
+        const float *hys = ys_tile ? HY : S + L::P + AH;
         constexpr int hxw = AW;
-        constexpr int hyw = kEdge ? TX : AW;
+        const int hyw = ys_tile ? TX : AW;
+        const bool build_h = xs_tile || ys_tile;   // CTA-uniform
 
         if (kEdge) {
             // ---- lam_h_x (own rows, x halo 8), lam_h_y (own columns, y halo 8)
-            if (ok && active) {
+            if (ok && active && build_h) {
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     const int v = tid + j * NTHREADS;   // 0 .. 767
                     if (v < TY * AW / 4) {
+                        if (!xs_tile)
+                            continue;
                         const int r = v / (AW / 4), c = 4 * (v % (AW / 4));
                         F4 h = ld4s(S + L::P + (r + AH) * AW + c);
                         const int x = x0 - AH + c, y = y0 + r;
@@ -413,6 +453,8 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                         }
                         st4s(HX + r * AW + c, h);
                     } else {
+                        if (!ys_tile)
+                            continue;
                         const int u = v - TY * AW / 4;  // 0 .. 383
                         const int r = u / (TX / 4), c = 4 * (u % (TX / 4));
                         F4 h = ld4s(S + L::P + r * AW + c + AH);
@@ -560,7 +602,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 st4s(A.gradK + o, gk);
             }
         }
-        if (kEdge)
+        if (kEdge && build_h)
             __syncthreads();   // the lam_h region becomes the lam_g region
         if (ok && active) {
             st4s(GX + ty * GW + 4 * tx + 4, gxo);

@@ -34,7 +34,7 @@
 // (read again 8 planes later) loaded evict-last, 4 = v_z and K (read once)
 // loaded evict-first
 #ifndef FDTD_L2HINT
-#define FDTD_L2HINT 0
+#define FDTD_L2HINT 1
 #endif
 // unroll factor of the z march (lets the compiler rename the queue registers)
 #ifndef FDTD_UNROLL

@@ -217,12 +217,13 @@ def test_energy_and_misfit_reductions_fp64():
     assert np.all(resid.cpu().numpy()[:, 4:] == 0)
 
 
-def test_interior_and_edge_chunkings_give_identical_state(monkeypatch):
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_interior_and_edge_chunkings_give_identical_state(monkeypatch, storage):
     """100 x 96 x 100, 24 shots: large enough that the default launch cuts z
     into one chunk per CPML end plus interior chunks (whose interior tiles run
     the kernel's interior form).  The state after 6 steps, with sources and
     receivers, equals bit for bit the one of uniform 7-plane chunks, where
-    every CTA runs the general form."""
+    every CTA runs the general form; FP32 and FP16 storage."""
     Fdtd = _fdtd()
     shape, cells, nshots, n = (100, 96, 100), (4, 5, 4, 6, 5, 4), 24, 6
     h, c = 10.0, 2500.0
@@ -238,7 +239,7 @@ def test_interior_and_edge_chunkings_give_identical_state(monkeypatch):
             monkeypatch.delenv("FDTD_ZCHUNK", raising=False)
         else:
             monkeypatch.setenv("FDTD_ZCHUNK", zc)
-        sim = Fdtd(shape, h, dt, nshots=nshots, cpml_cells=cells, nt_max=n, nrec_max=len(rec))
+        sim = Fdtd(shape, h, dt, nshots=nshots, cpml_cells=cells, nt_max=n, nrec_max=len(rec), storage=storage)
         sim.set_model(torch.from_numpy(vel).cuda())
         sim.set_cpml(R=1e-5, c_ref=c)
         sim.inject(src, torch.from_numpy(wav).cuda())

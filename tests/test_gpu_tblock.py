@@ -48,22 +48,24 @@ def _run(k, case, n, state=None, **kw):
     return sim, traces
 
 
-@pytest.mark.parametrize("k,band", [(2, "8"), (4, "8"), (2, None), (4, "11")])
-def test_blocked_steps_equal_single_steps_bitwise(monkeypatch, k, band):
+@pytest.mark.parametrize("k,band,storage", [(2, "8", "f32"), (4, "8", "f32"), (2, None, "f32"), (4, "11", "f32"),
+                                            (2, "8", "bf16")])
+def test_blocked_steps_equal_single_steps_bitwise(monkeypatch, k, band, storage):
     """45 x 70 x 75 (3 x 3 tiles with ragged tails; bands of 8 with a 13-plane
-    last band, or of 11, or the default 16), unequal CPML layers, two shots
-    with sources and receivers, a random initial state, and a step count that
-    leaves single steps after the last whole block."""
+    last band, or of 11, or the default 48, which is one band here), unequal
+    CPML layers, two shots with sources and receivers, a random initial
+    state, and a step count that leaves single steps after the last whole
+    block; FP32 and BF16 storage."""
     if band is not None:
         monkeypatch.setenv("FDTD_TBAND", band)
     case = _case((45, 70, 75), (4, 5, 3, 6, 5, 4), nshots=2, nt=24, seed=3)
     sc = state_scales(case["h"], case["dt"])
     state = [synth.random_state(case["shape"], case["cells"], seed=50 + s, **sc) for s in range(2)]
     n = 2 * k + 3
-    ref, tr_ref = _run(1, case, n, state)
+    ref, tr_ref = _run(1, case, n, state, storage=storage)
     ref.step(n)
     ref.sync()
-    sim, tr = _run(k, case, n, state)
+    sim, tr = _run(k, case, n, state, storage=storage)
     sim.step(n)
     sim.sync()
     assert sim.time == n
