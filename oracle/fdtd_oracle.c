@@ -46,7 +46,14 @@ typedef struct {
     const double *a[3];       /* CPML recursion coefficient a_d per node */
     const double *kinv[3];    /* 1/kappa_d per node */
     const unsigned char *slab[3]; /* 1 where the node lies in a d-slab */
+    const double *rho_n;      /* density per node [nz][ny][nx], or NULL: rho everywhere */
 } og_grid;
+
+/* density at node i (collocated with p and v, Sec. 3.1) */
+static double og_rho(const og_grid *g, long i)
+{
+    return g->rho_n ? g->rho_n[i] : g->rho;
+}
 
 typedef struct {
     double *p;
@@ -104,7 +111,7 @@ void og_velocity_stage(const og_grid *g, og_state *st)
                         st->psiv[d][i] = g->b[d][k] * st->psiv[d][i] + g->a[d][k] * gd;
                         gd = g->kinv[d][k] * gd + st->psiv[d][i];
                     }
-                    st->v[d][i] -= g->dt / g->rho * gd;
+                    st->v[d][i] -= g->dt / og_rho(g, i) * gd;
                 }
             }
 }
@@ -293,7 +300,7 @@ void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
                 long i = (z * ny + y) * nx + x;
                 for (int d = 0; d < 3; d++) {
                     long k = og_axis_index(d, z, y, x);
-                    double r = -g->dt / g->rho * adj->v[d][i];
+                    double r = -g->dt / og_rho(g, i) * adj->v[d][i];
                     if (g->slab[d][k]) {
                         double lpsi = adj->psiv[d][i] + r;
                         lam_g[d][i] = g->kinv[d][k] * r + g->a[d][k] * lpsi;

@@ -168,7 +168,7 @@ class _Grid(ctypes.Structure):
                 ("h", ctypes.c_double), ("dt", ctypes.c_double), ("rho", ctypes.c_double),
                 ("w", ctypes.c_double * 4), ("periodic", ctypes.c_int),
                 ("K", ctypes.c_void_p), ("b", _P3), ("a", _P3), ("kinv", _P3),
-                ("slab", _P3)]
+                ("slab", _P3), ("rho_n", ctypes.c_void_p)]
 
 
 class _State(ctypes.Structure):
@@ -227,7 +227,10 @@ class State:
 class Grid:
     """Grid, material and CPML description for the oracle.
 
-    K: bulk modulus K = rho c^2 per node (Sec. 3.1); rho: constant density.
+    K: bulk modulus K = rho c^2 per node (Sec. 3.1); rho: the density, a
+    constant or an array [nz][ny][nx] of per-node values (variable density,
+    collocated with p and v: the velocity update at a node uses dt / rho of
+    that node).
     Reading (Sec. 3.1 "normalized form"): physical units with rho given
     (1 in every workload here), velocity update scaled by dt/rho, pressure
     update by dt K, and each coefficient multiplies the whole CPML bracket.
@@ -236,7 +239,13 @@ class Grid:
     def __init__(self, K, h, dt, profiles=None, rho=1.0, periodic=False, weights=None):
         self.K = np.ascontiguousarray(K, dtype=np.float64)
         self.shape = self.K.shape
-        self.h, self.dt, self.rho = float(h), float(dt), float(rho)
+        self.h, self.dt = float(h), float(dt)
+        if np.ndim(rho) == 0:
+            self.rho, self.rho_n = float(rho), None
+        else:
+            self.rho = 1.0
+            self.rho_n = np.ascontiguousarray(rho, dtype=np.float64)
+            assert self.rho_n.shape == self.K.shape
         self.periodic = bool(periodic)
         self.weights = list(WEIGHTS if weights is None else weights)
         if profiles is None:
@@ -264,6 +273,7 @@ class Grid:
             g.a[d] = _ptr(pr["a"])
             g.kinv[d] = _ptr(pr["kinv"])
             g.slab[d] = _ptr(pr["slab"])
+        g.rho_n = _ptr(self.rho_n) if self.rho_n is not None else None
         return g
 
 
@@ -541,6 +551,7 @@ def standing_wave_state(shape, m, h, dt, rho, weights=None):
 def staggered_energy(grid: Grid, p_n, p_np1, v_half):
     """E^{n+1/2} = 1/2 sum rho |v^{n+1/2}|^2 + 1/2 sum p^n p^{n+1} / K, the
     discrete energy conserved by the leapfrog when D is skew-adjoint."""
-    ek = 0.5 * grid.rho * sum(float(np.sum(v * v)) for v in v_half)
+    rho = grid.rho if grid.rho_n is None else grid.rho_n
+    ek = 0.5 * sum(float(np.sum(rho * v * v)) for v in v_half)
     ep = 0.5 * float(np.sum(p_n * p_np1 / grid.K))
     return ek + ep
