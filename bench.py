@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--forms-only", action="store_true", help="measure only the forms (profiling runs)")
-    ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock",
+    ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock,density",
                     help="comma list of forms measured after the main line ('' for none)")
     return ap.parse_args()
 
@@ -350,6 +350,32 @@ def form_tblock(dev, nsteps=96, warm=8):
     return {"workload": f"layered512, {warm} + {nsteps} timed steps, z bands of 48 planes", "unit": UNIT, **out}
 
 
+def form_density(dev, nsteps=96, warm=8):
+    """Variable density on the 512^3 layered workload: density (c / 1500)^(1/4)
+    per node (a Gardner-type relation, dimensionless), against the same run
+    with density 1; Mpoints/s of both."""
+    import torch
+    from paper_2606_06910_gb300 import synth
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    w = synth.preset("layered512")
+    vel = torch.from_numpy(w.velocity()).to(dev)
+    rho = (vel / 1500.0) ** 0.25
+    npts = float(np.prod(w.shape))
+    out = {}
+    for name, r in (("constant", None), ("variable", rho)):
+        sim = Fdtd(w.shape, w.h, w.dt, cpml_cells=w.cpml_cells, nt_max=w.nt, device=dev)
+        sim.set_model(vel, r)
+        sim.set_cpml(R=w.R, c_ref=w.vmax)
+        sim.inject(w.sources(), torch.from_numpy(w.wavelet()).to(dev))
+        sim.step(warm)
+        sim.sync()
+        secs = _timed(sim.stream, lambda: sim.step(nsteps))
+        out[name] = {"value": round(npts * nsteps / secs / 1e6, 1), "ms_per_step": round(secs / nsteps * 1e3, 4)}
+        del sim
+        torch.cuda.empty_cache()
+    return {"workload": f"layered512, density (c/1500)^0.25, {warm} + {nsteps} timed steps", "unit": UNIT, **out}
+
+
 def form_adjoint(dev, nt=800, nshots=None, every=None):
     """Forward with checkpoints + discrete adjoint, 256^3 x 16 shots, 128x128
     receivers, checkpoint every 50 steps (gradient of the L2 misfit).  The form
@@ -554,6 +580,8 @@ def main():
                     forms[f] = form_learned(dev)
                 elif f == "tblock":
                     forms[f] = form_tblock(dev)
+                elif f == "density":
+                    forms[f] = form_density(dev)
             except Exception as e:  # report, keep the main line
                 forms[f] = {"error": f"{type(e).__name__}: {e}"[:300]}
         out["forms"] = forms

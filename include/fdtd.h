@@ -118,10 +118,14 @@ int fdtd_destroy(fdtd_ctx *ctx);
 /* One-line description of the last failure on this context ("" if none). */
 const char *fdtd_last_error(const fdtd_ctx *ctx);
 
-/* Velocity model (paper Sec. 3.1: K = rho c^2).  vel_dev: float [nz][ny][nx]
- * in m/s, read during the call.  rho_dev must be NULL (constant density 1;
- * variable density is not provided: EUNSUPPORTED).  Synchronises; EINVAL if a
- * velocity is not finite and positive; EUNSTABLE if max(c) dt / h exceeds the
+/* Velocity model (paper Sec. 3.1: p_t = -K div v, v_t = -(1/rho) grad p,
+ * K = rho c^2).  vel_dev: float [nz][ny][nx] in m/s; rho_dev: NULL (density 1
+ * everywhere) or float [nz][ny][nx], the density per node, collocated with p
+ * and v (the velocity update at a node uses dt / rho of that node).  Both are
+ * read during the call.  With a density the step reads one more table
+ * (4 B per node, shared by the shots) and the adjoint is not provided
+ * (fdtd_adjoint_step_n: EUNSUPPORTED).  Synchronises; EINVAL if a velocity or
+ * density is not finite and positive; EUNSTABLE if max(c) dt / h exceeds the
  * collocated radius-4 leapfrog limit 2 / (sqrt(3) max_theta 2 sum_l a_l sin(l theta)) = 0.6672. */
 int fdtd_set_model(fdtd_ctx *ctx, const float *vel_dev, const float *rho_dev);
 
@@ -182,7 +186,8 @@ int fdtd_step_n(fdtd_ctx *ctx, int n);
  * [b, a, 1/kappa][node]) receives += dJ/d(profile) and needs cpml_grad at
  * create time (EINVAL otherwise).  Needs FP32 storage,
  * checkpoint_every > 0 and n equal to the current time index (ESTATE
- * otherwise).  Leaves the forward state undefined (call fdtd_reset). */
+ * otherwise), and a model without density (EUNSUPPORTED otherwise).  Leaves
+ * the forward state undefined (call fdtd_reset). */
 int fdtd_adjoint_step_n(fdtd_ctx *ctx, int n, const float *resid_dev,
                         float *grad_vel_dev, float *grad_cpml_dev);
 

@@ -16,7 +16,7 @@
 namespace fdtd {
 cudaError_t launch_step(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream);
 int step_occupancy(int storage, int *blocks);
-cudaError_t launch_model(fdtd_ctx *c, const float *vel);
+cudaError_t launch_model(fdtd_ctx *c, const float *vel, const float *rho);
 cudaError_t launch_field(const fdtd_ctx *c, bool get, void *internal, float *dense, int kind, float scale,
                          bool is_f32, const float *kscale);
 cudaError_t launch_energy(const fdtd_ctx *c, const void *p, const int *box);
@@ -66,7 +66,7 @@ struct Layout {
     int es;
     int tiles_x, tiles_y;
     size_t p[2], v[3][2], psiv[3][2], psip[3];
-    size_t kdt, coef, wav, src, rec, rec_off, err, red, minmax;
+    size_t kdt, nbr, coef, wav, src, rec, rec_off, err, red, minmax;
     int ncp;
     size_t ckpt, ckpt_slot, tape_s, tape_slab[3], ap[2], av[3][2], apsiv[3][2], apsip[3][2], gradK, gprof;
     size_t total;
@@ -149,6 +149,7 @@ void make_layout(const fdtd_desc *d, Layout *L)
         L->psip[a] = take(S * g.slab[a] * L->es);
     }
     L->kdt = take((size_t)g.vol * 4);
+    L->nbr = take((size_t)g.vol * 4);
     L->coef = take((size_t)9 * nmax_of(g) * 4);
     L->wav = take(S * d->nt_max * 4);
     L->src = take(S * 3 * 4);
@@ -455,6 +456,7 @@ StepArgs base_args(const fdtd_ctx *c)
     for (int l = 0; l < 4; ++l)
         a.c[l] = (float)(kWeights[l] / c->d.h);
     a.dtr = (float)(c->d.dt * c->vscale);   // rho = 1
+    a.nbr = c->var_rho ? c->nbr : nullptr;
     a.sscale = c->sscale;
     a.inv_sscale = 1.f / c->sscale;
     a.src = c->nt_w > 0 ? c->src : nullptr;
@@ -715,6 +717,7 @@ int fdtd_create(const fdtd_desc *desc, void *workspace, size_t workspace_bytes, 
         c->psip[d] = w + L.psip[d];
     }
     c->kdt = (float *)(w + L.kdt);
+    c->nbr = (float *)(w + L.nbr);
     c->coef = (float *)(w + L.coef);
     c->wavelet = (float *)(w + L.wav);
     c->src = (int *)(w + L.src);
@@ -788,15 +791,14 @@ int fdtd_set_model(fdtd_ctx *c, const float *vel, const float *rho)
 {
     if (!c || !vel)
         return fail(c, FDTD_EINVAL, "vel is NULL");
-    if (rho)
-        return fail(c, FDTD_EUNSUPPORTED, "variable density is not provided (rho must be NULL)");
     unsigned mm[3];
     c->vscale = 1.f;
-    CUDA_TRY(c, launch_model(c, vel));
+    c->model_set = false;
+    CUDA_TRY(c, launch_model(c, vel, rho));
     CUDA_TRY(c, cudaMemcpyAsync(mm, c->minmax, sizeof(mm), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (mm[2] != 0)
-        return fail(c, FDTD_EINVAL, "%u velocities are not finite and positive", mm[2]);
+        return fail(c, FDTD_EINVAL, "%u nodes have a velocity or density that is not finite and positive", mm[2]);
     float vmin, vmax;
     memcpy(&vmin, &mm[0], 4);
     memcpy(&vmax, &mm[1], 4);
@@ -809,8 +811,9 @@ int fdtd_set_model(fdtd_ctx *c, const float *vel, const float *rho)
     if (c->d.storage != FDTD_F32) {
         // impedance scaling keeps the stored velocities O(p) in 16-bit
         c->vscale = vmax;
-        CUDA_TRY(c, launch_model(c, vel));
+        CUDA_TRY(c, launch_model(c, vel, rho));
     }
+    c->var_rho = rho != nullptr;
     c->model_set = true;
     return FDTD_OK;
 }
@@ -1001,6 +1004,8 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
         return fail(c, FDTD_ESTATE, "n must equal the current time index (%d) and be <= nt_max", c->t);
     if (grad_cpml && !c->d.cpml_grad)
         return fail(c, FDTD_EINVAL, "grad_cpml needs cpml_grad at create time");
+    if (c->var_rho)
+        return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for constant density (rho = 1) only");
     const bool want_prof = grad_cpml != nullptr;
     const int nmax = nmax_of(c->g);
     CUDA_TRY(c, cudaMemsetAsync(c->gradK, 0, (size_t)c->d.nshots * c->g.vol * 4, c->stream));

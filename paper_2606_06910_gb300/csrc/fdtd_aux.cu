@@ -9,8 +9,10 @@ namespace fdtd {
 // ---------------------------------------------------------------------------
 // model: kdt = -dt K / vscale with K = rho c^2 (rho = 1); min / max / invalid
 // ---------------------------------------------------------------------------
-__global__ void model_kernel(const float *__restrict__ vel, float *__restrict__ kdt, Geom g, double dt_over_vs,
-                             unsigned *minmax)
+// kdt = -dt rho c^2 / vscale (K = rho c^2) and, with a density, nbr = -dt
+// vscale / rho, per node (0 in the row padding); rho = 1 without one.
+__global__ void model_kernel(const float *__restrict__ vel, const float *__restrict__ rho, float *__restrict__ kdt,
+                             float *__restrict__ nbr, Geom g, double dt, double vs, unsigned *minmax)
 {
     const long long n = g.vol;
     unsigned vmin = 0x7f800000u, vmax = 0u, bad = 0u;
@@ -20,15 +22,22 @@ __global__ void model_kernel(const float *__restrict__ vel, float *__restrict__ 
         const long long zy = i / g.nxp;
         if (x >= g.nx) {
             kdt[i] = 0.f;
+            if (rho)
+                nbr[i] = 0.f;
             continue;
         }
         const float c = vel[zy * g.nx + x];
-        if (!(c > 0.f) || !isfinite(c)) {
+        const float r = rho ? rho[zy * g.nx + x] : 1.f;
+        if (!(c > 0.f) || !isfinite(c) || !(r > 0.f) || !isfinite(r)) {
             bad++;
             kdt[i] = 0.f;
+            if (rho)
+                nbr[i] = 0.f;
             continue;
         }
-        kdt[i] = (float)(-dt_over_vs * (double)c * (double)c);
+        kdt[i] = (float)(-(dt / vs) * (double)r * (double)c * (double)c);
+        if (rho)
+            nbr[i] = (float)(-(dt * vs) / (double)r);
         const unsigned b = __float_as_uint(c);   // positive floats order like unsigned ints
         vmin = min(vmin, b);
         vmax = max(vmax, b);
@@ -39,13 +48,13 @@ __global__ void model_kernel(const float *__restrict__ vel, float *__restrict__ 
         atomicAdd(&minmax[2], bad);
 }
 
-cudaError_t launch_model(fdtd_ctx *c, const float *vel)
+cudaError_t launch_model(fdtd_ctx *c, const float *vel, const float *rho)
 {
     const unsigned init[3] = {0x7f800000u, 0u, 0u};
     cudaError_t e = cudaMemcpyAsync(c->minmax, init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess)
         return e;
-    model_kernel<<<1216, 256, 0, c->stream>>>(vel, c->kdt, c->g, c->d.dt / c->vscale, c->minmax);
+    model_kernel<<<1216, 256, 0, c->stream>>>(vel, rho, c->kdt, c->nbr, c->g, c->d.dt, c->vscale, c->minmax);
     return cudaGetLastError();
 }
 

@@ -348,7 +348,8 @@ struct StepArgs {
     void *psip[3];                  // updated in place
     const float *cb[3], *ca[3], *ck[3];   // b, a, 1/kappa per node of each axis
     float c[4];                     // a_l / h
-    float dtr;                      // dt * vscale / rho (velocity update)
+    float dtr;                      // dt * vscale / rho (velocity update, constant density)
+    const float *nbr;               // [vol] -dt * vscale / rho per node (variable density), or null
     float sscale, inv_sscale;       // stored state = sscale * physical state
     const int *src;                 // [nshots][3] (z, y, x)
     const float *wavelet;           // [nshots][nt_w]
@@ -385,6 +386,8 @@ struct fdtd_ctx {
     size_t ws_bytes;
     void *p[2], *v[3][2], *psiv[3][2], *psip[3];
     float *kdt;             // -dt K / vscale per node [nz][ny][nxp] (0 in the row padding)
+    float *nbr;             // -dt vscale / rho per node (variable density), same layout
+    bool var_rho;           // fdtd_set_model was given a density
     float *coef;            // [3][3][nmax]: b, a, 1/kappa per axis and node
     float *wavelet;         // [nshots][nt_max]
     int nt_w;

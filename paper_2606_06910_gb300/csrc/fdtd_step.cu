@@ -223,6 +223,18 @@ __device__ __forceinline__ V4 cpml4(V4 &g, const V4 &psi, const V4 &b, const V4 
 
 __device__ __forceinline__ V4 splat4(float s) { return V4{make_float2(s, s), make_float2(s, s)}; }
 
+// x + s y with a per-node factor s (variable density)
+__device__ __forceinline__ V4 fmav(const V4 &s, const V4 &x, const V4 &y)
+{
+    return V4{fma2(s.a, x.a, y.a), fma2(s.b, x.b, y.b)};
+}
+
+// -dt vscale / rho of 4 nodes (0 when the row is outside the grid)
+__device__ __forceinline__ V4 ld_nbr(const float *nbr, long long o, bool ok)
+{
+    return ok ? to_v4(Io<float>::ldg4(nbr + o)) : v4zero();
+}
+
 template <typename T>
 __device__ __forceinline__ V4 ldg_v4(const T *p) { return to_v4(Io<T>::ld4(p)); }
 
@@ -301,7 +313,7 @@ __host__ __device__ __forceinline__ int chunk_count(const StepArgs &A)
 // inside the grid and outside every CPML slab, so it needs no memory
 // variables, no coefficient tables and no masks at the grid edge.  The same
 // arithmetic in the same order runs in both forms.
-template <typename T, bool kEdge>
+template <typename T, bool kEdge, bool kRho>
 __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorMap &mPq, const CUtensorMap &mVX,
                                           const CUtensorMap &mVY, const CUtensorMap &mVZ, const CUtensorMap &mK,
                                           const StepArgs &A, int z0, int z1, unsigned char *smem,
@@ -503,6 +515,33 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
             }
         }
 
+        // -dt vscale / rho (variable density): this plane's factors are
+        // loaded before the wait, so that their latency overlaps it, and the
+        // next plane's go into L2
+        V4 nbo = v4zero(), nbz = v4zero();
+        float2 nbh = make_float2(0.f, 0.f);
+        if (kRho) {
+            if (t >= z0)
+                nbo = ld_nbr(A.nbr, (long long)t * G.plane + rowofs, row_ok);
+            if (zv >= 0 && zv < G.nz)
+                nbz = ld_nbr(A.nbr, (long long)zv * G.plane + rowofs, row_ok);
+            if (t >= z0) {
+                const int hy = do_yhalo ? yh_y : xh_y, hx = do_yhalo ? yh_x : xh_x;
+                const bool hin = do_yhalo ? (yh_in && yh_x < G.nxp) : (xh_y < G.ny && xh_x >= 0 && xh_x < G.nxp);
+                const long long ho = (long long)hy * G.nxp + hx;
+                if (hin) {
+                    nbh = __ldg(reinterpret_cast<const float2 *>(A.nbr + (long long)t * G.plane + ho));
+                    if (t + 1 < z1)
+                        prefetch_l2(A.nbr + (long long)(t + 1) * G.plane + ho);
+                }
+            }
+            if (row_ok) {
+                if (t + 1 >= z0 && t + 1 < z1)
+                    prefetch_l2(A.nbr + (long long)(t + 1) * G.plane + rowofs);
+                if (zv + 1 >= 0 && zv + 1 < G.nz)
+                    prefetch_l2(A.nbr + (long long)(zv + 1) * G.plane + rowofs);
+            }
+        }
         const bool ok = mbar_wait_bounded(&bar[it % NSTAGE], (it / NSTAGE) & 1, WAIT_LIMIT);
 
         // ---- z block: p(t + 8) into the queue (TMA zero-fills nodes beyond the
@@ -523,7 +562,10 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     if (owned)
                         st_out(psiv_out[2] + izv, to_f4(pn));
                 }
-                vzn = fma4(ndtr, gz, lds<T>(S + L::OFF_VZ, ty * TX + 4 * tx));
+                if (kRho)
+                    vzn = fmav(nbz, gz, lds<T>(S + L::OFF_VZ, ty * TX + 4 * tx));
+                else
+                    vzn = fma4(ndtr, gz, lds<T>(S + L::OFF_VZ, ty * TX + 4 * tx));
                 if (owned && row_ok)
                     st_out(v_out[2] + (long long)zv * G.plane + rowofs, to_f4(vzn));
             }
@@ -548,7 +590,8 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     const V4 pn = cpml4(g, psvx, ldsf(&sCx[0][cx]), ldsf(&sCx[1][cx]), ldsf(&sCx[2][cx]));
                     st_out(psiv_out[0] + ix, to_f4(pn));
                 }
-                V4 vn = fma4(ndtr, g, lds<T>(S + L::OFF_VX, ty * L::VXW + 4 * tx + 8));
+                V4 vn = kRho ? fmav(nbo, g, lds<T>(S + L::OFF_VX, ty * L::VXW + 4 * tx + 8))
+                             : fma4(ndtr, g, lds<T>(S + L::OFF_VX, ty * L::VXW + 4 * tx + 8));
                 if (!full_tile)
                     vn = mul4(vn, mask);
                 if (row_ok)
@@ -573,7 +616,8 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     const V4 pn = cpml4(g, psvy, splat4(sCy[0][ty + 4]), splat4(sCy[1][ty + 4]), splat4(sCy[2][ty + 4]));
                     st_out(psiv_out[1] + iy, to_f4(pn));
                 }
-                V4 vn = fma4(ndtr, g, lds<T>(S + L::OFF_VY, (ty + 4) * TX + 4 * tx));
+                V4 vn = kRho ? fmav(nbo, g, lds<T>(S + L::OFF_VY, (ty + 4) * TX + 4 * tx))
+                             : fma4(ndtr, g, lds<T>(S + L::OFF_VY, (ty + 4) * TX + 4 * tx));
                 if (!full_tile)
                     vn = mul4(vn, mask);
                 if (row_ok)
@@ -596,7 +640,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     cpml2(g, psh, make_float2(sCy[0][r], sCy[0][r]), make_float2(sCy[1][r], sCy[1][r]),
                           make_float2(sCy[2][r], sCy[2][r]));
                 }
-                float2 vn = fma2(ndtr, g, lds2<T>(S + L::OFF_VY, r * TX + (yh_x - x0)));
+                float2 vn = fma2(kRho ? nbh : ndtr, g, lds2<T>(S + L::OFF_VY, r * TX + (yh_x - x0)));
                 if (kEdge) {
                     vn.x = (yh_in && yh_x < G.nx) ? vn.x : 0.f;
                     vn.y = (yh_in && yh_x + 1 < G.nx) ? vn.y : 0.f;
@@ -612,7 +656,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     cpml2(g, psh, *reinterpret_cast<const float2 *>(&sCx[0][cx]),
                           *reinterpret_cast<const float2 *>(&sCx[1][cx]), *reinterpret_cast<const float2 *>(&sCx[2][cx]));
                 }
-                float2 vn = fma2(ndtr, g, lds2<T>(S + L::OFF_VX, (xh_y - y0) * L::VXW + lx));
+                float2 vn = fma2(kRho ? nbh : ndtr, g, lds2<T>(S + L::OFF_VX, (xh_y - y0) * L::VXW + lx));
                 if (kEdge) {
                     vn.x = (xh_y < G.ny && xh_x >= 0 && xh_x < G.nx) ? vn.x : 0.f;
                     vn.y = (xh_y < G.ny && xh_x + 1 >= 0 && xh_x + 1 < G.nx) ? vn.y : 0.f;
@@ -714,7 +758,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
     }
 }
 
-template <typename T>
+template <typename T, bool kRho>
 __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
     fdtd_step_kernel(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mPq,
                      const __grid_constant__ CUtensorMap mVX, const __grid_constant__ CUtensorMap mVY,
@@ -733,27 +777,34 @@ __global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
     const bool interior = x0 - 4 >= G.lo[0] && x0 + TX + 4 <= G.nx - G.hi[0] && y0 - 4 >= G.lo[1] &&
                           y0 + TY + 4 <= G.ny - G.hi[1] && z0 - 4 >= G.lo[2] && z1 + 4 <= G.nz - G.hi[2];
     if (interior)
-        step_body<T, false>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy);
+        step_body<T, false, kRho>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy);
     else
-        step_body<T, true>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy);
+        step_body<T, true, kRho>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy);
 }
 
-template <typename T>
-static cudaError_t launch_step_t(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream)
+template <typename T, bool kRho>
+static cudaError_t launch_step_tr(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream)
 {
     using L = StageLayout<T>;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(fdtd_step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             L::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(fdtd_step_kernel<T, kRho>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
         if (e != cudaSuccess)
             return e;
         attr_done = true;
     }
     dim3 grid(c->tiles_x * c->tiles_y, chunk_count(a), c->d.nshots);
-    fdtd_step_kernel<T><<<grid, NTHREADS, L::SMEM, stream>>>(c->maps[set][0], c->maps[set][1], c->maps[set][2],
-                                                              c->maps[set][3], c->maps[set][4], c->mapK, a);
+    fdtd_step_kernel<T, kRho><<<grid, NTHREADS, L::SMEM, stream>>>(
+        c->maps[set][0], c->maps[set][1], c->maps[set][2], c->maps[set][3], c->maps[set][4], c->mapK, a);
     return cudaGetLastError();
+}
+
+// a.nbr selects the variable-density form
+template <typename T>
+static cudaError_t launch_step_t(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream)
+{
+    return a.nbr ? launch_step_tr<T, true>(c, a, set, stream) : launch_step_tr<T, false>(c, a, set, stream);
 }
 
 // One step over z in [a.zbase, a.zend) on `stream`; `set` is the ping-pong
@@ -774,8 +825,8 @@ template <typename T>
 static int occupancy_t(int *blocks)
 {
     using L = StageLayout<T>;
-    cudaFuncSetAttribute(fdtd_step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fdtd_step_kernel<T>, NTHREADS, L::SMEM) ==
+    cudaFuncSetAttribute(fdtd_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fdtd_step_kernel<T, false>, NTHREADS, L::SMEM) ==
                    cudaSuccess
                ? 0
                : -1;

@@ -114,9 +114,12 @@ class Fdtd:
             raise FdtdError(status, msg)
 
     # -- set-up --------------------------------------------------------------
-    def set_model(self, vel: torch.Tensor):
+    def set_model(self, vel: torch.Tensor, rho: torch.Tensor | None = None):
+        """Velocity [m/s] and, optionally, density per node (both [nz, ny, nx])."""
         _need(vel, self.shape, self.device, "vel")
-        self._check(self.lib.fdtd_set_model(self.ctx, _ptr(vel), None))
+        if rho is not None:
+            _need(rho, self.shape, self.device, "rho")
+        self._check(self.lib.fdtd_set_model(self.ctx, _ptr(vel), _ptr(rho)))
 
     def set_cpml(self, R=1e-8, kappa_max=5.0, alpha_frac=0.05, q=3, c_ref=None):
         self._check(self.lib.fdtd_set_cpml(self.ctx, float(R), float(kappa_max), float(alpha_frac),
