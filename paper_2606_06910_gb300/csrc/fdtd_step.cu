@@ -21,29 +21,10 @@
 // 1/kappa = 1 outside the slabs.
 #include "fdtd_internal.cuh"
 
-#ifndef FDTD_PACKED
-#define FDTD_PACKED 1
-#endif
-#ifndef FDTD_MINB
-#define FDTD_MINB 2
-#endif
-#ifndef FDTD_PREFETCH
-#define FDTD_PREFETCH 1
-#endif
-// L2 policy bits: 1 = outputs stored evict-first, 2 = the z-queue plane of p
-// (read again 8 planes later) loaded evict-last, 4 = v_z and K (read once)
-// loaded evict-first
-#ifndef FDTD_L2HINT
-#define FDTD_L2HINT 1
-#endif
-// unroll factor of the z march (lets the compiler rename the queue registers)
-#ifndef FDTD_UNROLL
-#define FDTD_UNROLL 1
-#endif
-
 namespace fdtd {
 
-constexpr int kZUnroll = FDTD_UNROLL;
+// 2 CTAs of 256 threads per SM (128 registers per thread)
+constexpr int kMinBlocks = 2;
 
 template <typename T>
 struct StageLayout {
@@ -81,18 +62,9 @@ struct V4 {
 __device__ __forceinline__ V4 v4zero() { return V4{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
 __device__ __forceinline__ V4 to_v4(const F4 &f) { return V4{make_float2(f.v[0], f.v[1]), make_float2(f.v[2], f.v[3])}; }
 __device__ __forceinline__ F4 to_f4(const V4 &v) { return F4{{v.a.x, v.a.y, v.b.x, v.b.y}}; }
-#if FDTD_PACKED
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-#else
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
-{
-    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-#endif
 __device__ __forceinline__ V4 fma4(float2 s, const V4 &x, const V4 &y) { return V4{fma2(s, x.a, y.a), fma2(s, x.b, y.b)}; }
 __device__ __forceinline__ V4 mul4(const V4 &x, const V4 &y) { return V4{mul2(x.a, y.a), mul2(x.b, y.b)}; }
 __device__ __forceinline__ V4 add4(const V4 &x, const V4 &y) { return V4{add2(x.a, y.a), add2(x.b, y.b)}; }
@@ -238,14 +210,11 @@ __device__ __forceinline__ V4 ld_nbr(const float *nbr, long long o, bool ok)
 template <typename T>
 __device__ __forceinline__ V4 ldg_v4(const T *p) { return to_v4(Io<T>::ld4(p)); }
 
-// store of a step output (not read again within this step)
+// store of a step output, not read again within this step: L2 evict-first
 template <typename T>
 __device__ __forceinline__ void st_out(T *p, const F4 &v)
 {
-    if (FDTD_L2HINT & 1)
-        Io<T>::st4s(p, v);
-    else
-        Io<T>::st4(p, v);
+    Io<T>::st4s(p, v);
 }
 
 // tape (g, psi_old) of 4 nodes into slots [idx*4 + off, +1]
@@ -423,8 +392,6 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
     }
     __syncthreads();
 
-    const uint64_t pol_first = (FDTD_L2HINT & 4) ? l2_evict_first() : 0;
-    const uint64_t pol_last = (FDTD_L2HINT & 2) ? l2_evict_last() : 0;
     // Issue the loads of iteration `it` into its stage (thread 0 only).
     auto issue = [&](int it) {
         const int t = z0 - 8 + it;
@@ -438,26 +405,15 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
         bytes += vz_on ? L::VZ_BYTES : 0;
         bytes += main_on ? (L::P_BYTES + L::VX_BYTES + L::VY_BYTES + L::K_BYTES) : 0;
         mbar_arrive_expect_tx(b, bytes);
-        if (q_on) {
-            if (FDTD_L2HINT & 2)
-                tma_load_4d_hint(S + L::OFF_PQ, &mPq, b, x0, y0, t + 8, shot, pol_last);
-            else
-                tma_load_4d(S + L::OFF_PQ, &mPq, b, x0, y0, t + 8, shot);
-        }
-        if (vz_on) {
-            if (FDTD_L2HINT & 4)
-                tma_load_4d_hint(S + L::OFF_VZ, &mVZ, b, x0, y0, t + 4, shot, pol_first);
-            else
-                tma_load_4d(S + L::OFF_VZ, &mVZ, b, x0, y0, t + 4, shot);
-        }
+        if (q_on)
+            tma_load_4d(S + L::OFF_PQ, &mPq, b, x0, y0, t + 8, shot);
+        if (vz_on)
+            tma_load_4d(S + L::OFF_VZ, &mVZ, b, x0, y0, t + 4, shot);
         if (main_on) {
             tma_load_4d(S + L::OFF_P, &mP, b, x0 - 8, y0 - 8, t, shot);
             tma_load_4d(S + L::OFF_VX, &mVX, b, x0 - 8, y0, t, shot);
             tma_load_4d(S + L::OFF_VY, &mVY, b, x0, y0 - 4, t, shot);
-            if (FDTD_L2HINT & 4)
-                tma_load_3d_hint(S + L::OFF_K, &mK, b, x0, y0, t, pol_first);
-            else
-                tma_load_3d(S + L::OFF_K, &mK, b, x0, y0, t);
+            tma_load_3d(S + L::OFF_K, &mK, b, x0, y0, t);
         }
     };
     if (tid == 0)
@@ -477,7 +433,6 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
     pq[8] = v4zero();
     vzq[8] = v4zero();
 
-#pragma unroll kZUnroll
     for (int it = 0; it < niter; ++it) {
         const int t = z0 - 8 + it;
         const int zv = t + 4;
@@ -489,7 +444,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
 
         // L2 prefetch of the memory variables of the next plane, so that the
         // slab loads of the next iteration do not wait on HBM
-        if (FDTD_PREFETCH && kEdge) {
+        if (kEdge) {
             const int tn = t + 1, zn = zv + 1;
             if (row_ok && zn < G.nz && zn >= 0 && in_slab(zn, G.nz, G.lo[2], G.hi[2]))
                 prefetch_l2(psiv_in[2] + slab_index(G, 2, zn, gy, gx));
@@ -759,7 +714,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
 }
 
 template <typename T, bool kRho>
-__global__ void __launch_bounds__(NTHREADS, FDTD_MINB)
+__global__ void __launch_bounds__(NTHREADS, kMinBlocks)
     fdtd_step_kernel(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mPq,
                      const __grid_constant__ CUtensorMap mVX, const __grid_constant__ CUtensorMap mVY,
                      const __grid_constant__ CUtensorMap mVZ, const __grid_constant__ CUtensorMap mK,
