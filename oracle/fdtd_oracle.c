@@ -47,6 +47,7 @@ typedef struct {
     const double *kinv[3];    /* 1/kappa_d per node */
     const unsigned char *slab[3]; /* 1 where the node lies in a d-slab */
     const double *rho_n;      /* density per node [nz][ny][nx], or NULL: rho everywhere */
+    double kr[3];             /* elliptic anisotropy: modulus along axis d = kr[d] K (1 = isotropic) */
 } og_grid;
 
 /* density at node i (collocated with p and v, Sec. 3.1) */
@@ -136,7 +137,7 @@ void og_pressure_stage(const og_grid *g, og_state *st, double *s_out)
                         st->psip[d][i] = g->b[d][k] * st->psip[d][i] + g->a[d][k] * hd;
                         hd = g->kinv[d][k] * hd + st->psip[d][i];
                     }
-                    s += hd;
+                    s += g->kr[d] * hd;
                 }
                 st->p[i] -= g->dt * g->K[i] * s;
                 if (s_out)

@@ -168,7 +168,7 @@ class _Grid(ctypes.Structure):
                 ("h", ctypes.c_double), ("dt", ctypes.c_double), ("rho", ctypes.c_double),
                 ("w", ctypes.c_double * 4), ("periodic", ctypes.c_int),
                 ("K", ctypes.c_void_p), ("b", _P3), ("a", _P3), ("kinv", _P3),
-                ("slab", _P3), ("rho_n", ctypes.c_void_p)]
+                ("slab", _P3), ("rho_n", ctypes.c_void_p), ("kr", ctypes.c_double * 3)]
 
 
 class _State(ctypes.Structure):
@@ -227,6 +227,10 @@ class State:
 class Grid:
     """Grid, material and CPML description for the oracle.
 
+    kr: elliptic anisotropy, (x, y, z) factors of the modulus in the
+    pressure update, p' = p - dt K sum_d kr_d [...]_d; the axis velocities are
+    c sqrt(kr_d) (the 2D demo of Sec. 5 has c_x = 2600, c_z = 1800 m/s).  The
+    transpose (adjoint_step) is for kr = (1, 1, 1) only.
     K: bulk modulus K = rho c^2 per node (Sec. 3.1); rho: the density, a
     constant or an array [nz][ny][nx] of per-node values (variable density,
     collocated with p and v: the velocity update at a node uses dt / rho of
@@ -236,7 +240,7 @@ class Grid:
     update by dt K, and each coefficient multiplies the whole CPML bracket.
     """
 
-    def __init__(self, K, h, dt, profiles=None, rho=1.0, periodic=False, weights=None):
+    def __init__(self, K, h, dt, profiles=None, rho=1.0, periodic=False, weights=None, kr=(1.0, 1.0, 1.0)):
         self.K = np.ascontiguousarray(K, dtype=np.float64)
         self.shape = self.K.shape
         self.h, self.dt = float(h), float(dt)
@@ -247,6 +251,7 @@ class Grid:
             self.rho_n = np.ascontiguousarray(rho, dtype=np.float64)
             assert self.rho_n.shape == self.K.shape
         self.periodic = bool(periodic)
+        self.kr = tuple(float(r) for r in kr)   # (x, y, z): axis moduli kr_d K
         self.weights = list(WEIGHTS if weights is None else weights)
         if profiles is None:
             profiles = no_cpml_profiles(self.shape)
@@ -274,6 +279,8 @@ class Grid:
             g.kinv[d] = _ptr(pr["kinv"])
             g.slab[d] = _ptr(pr["slab"])
         g.rho_n = _ptr(self.rho_n) if self.rho_n is not None else None
+        for d in range(3):
+            g.kr[d] = self.kr[d]
         return g
 
 
@@ -549,9 +556,10 @@ def standing_wave_state(shape, m, h, dt, rho, weights=None):
 
 
 def staggered_energy(grid: Grid, p_n, p_np1, v_half):
-    """E^{n+1/2} = 1/2 sum rho |v^{n+1/2}|^2 + 1/2 sum p^n p^{n+1} / K, the
-    discrete energy conserved by the leapfrog when D is skew-adjoint."""
+    """E^{n+1/2} = 1/2 sum_d kr_d rho |v_d^{n+1/2}|^2 + 1/2 sum p^n p^{n+1} / K,
+    the discrete energy conserved by the leapfrog when D is skew-adjoint
+    (kr: the grid's anisotropy factors, 1 when isotropic)."""
     rho = grid.rho if grid.rho_n is None else grid.rho_n
-    ek = 0.5 * sum(float(np.sum(rho * v * v)) for v in v_half)
+    ek = 0.5 * sum(kr * float(np.sum(rho * v * v)) for kr, v in zip(grid.kr, v_half))
     ep = 0.5 * float(np.sum(p_n * p_np1 / grid.K))
     return ek + ep
