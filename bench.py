@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--forms-only", action="store_true", help="measure only the forms (profiling runs)")
-    ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock,density",
+    ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock,density,aniso2d",
                     help="comma list of forms measured after the main line ('' for none)")
     return ap.parse_args()
 
@@ -376,6 +376,23 @@ def form_density(dev, nsteps=96, warm=8):
     return {"workload": f"layered512, density (c/1500)^0.25, {warm} + {nsteps} timed steps", "unit": UNIT, **out}
 
 
+def form_aniso2d(dev, nt=1000, every=50):
+    """The paper's 2D anisotropic CPML demonstration (Sec. 5): sum p^2 inside
+    the layer relative to its peak, with a 10-cell layer and with none."""
+    from paper_2606_06910_gb300 import demos
+    t0 = time.perf_counter()
+    _, e_c, cfg, _ = demos.anisotropic_2d(True, nt, every, device=dev)
+    secs = time.perf_counter() - t0
+    _, e_n, _, _ = demos.anisotropic_2d(False, nt, every, device=dev)
+    dt = cfg["dt"]
+    curve = {f"{(k + 1) * every * dt:.3f}s": [float(f"{e_c[k] / e_c.max():.3e}"), float(f"{e_n[k] / e_n.max():.3e}")]
+             for k in range(0, len(e_c), 4)}
+    return {"workload": f"2 km x 2 km, 8 m, c_x 2600 / c_z 1800 m/s, 30 Hz, {nt} steps",
+            "final_over_peak_cpml": float(f"{e_c[-1] / e_c.max():.3e}"),
+            "final_over_peak_no_cpml": float(f"{e_n[-1] / e_n.max():.3e}"),
+            "curve_cpml_vs_none": curve, "wall_s_cpml_run": round(secs, 3)}
+
+
 def form_adjoint(dev, nt=800, nshots=None, every=None):
     """Forward with checkpoints + discrete adjoint, 256^3 x 16 shots, 128x128
     receivers, checkpoint every 50 steps (gradient of the L2 misfit).  The form
@@ -582,6 +599,8 @@ def main():
                     forms[f] = form_tblock(dev)
                 elif f == "density":
                     forms[f] = form_density(dev)
+                elif f == "aniso2d":
+                    forms[f] = form_aniso2d(dev)
             except Exception as e:  # report, keep the main line
                 forms[f] = {"error": f"{type(e).__name__}: {e}"[:300]}
         out["forms"] = forms

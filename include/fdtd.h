@@ -140,6 +140,19 @@ int fdtd_set_model(fdtd_ctx *ctx, const float *vel_dev, const float *rho_dev);
 int fdtd_set_cpml(fdtd_ctx *ctx, double R, double kappa_max, double alpha_frac,
                   int q, double c_ref);
 
+/* Elliptic anisotropy (the acoustic system of the paper's 2D CPML
+ * demonstration, Sec. 5): the pressure update becomes
+ *   p <- p - dt K sum_d kr_d [ (1/kappa_d) delta_d v_d + psi_{p,d} ],
+ * so the wave speed along axis d is c sqrt(kr_d).  kr (host double[3],
+ * x, y, z) must be finite and positive; (1, 1, 1) is the isotropic default.
+ * The stability limit becomes c_max dt / h <= 2 / (sqrt(sum_d kr_d) max_theta
+ * 2 sum_l a_l sin(l theta)); EUNSTABLE (factors unchanged) if a set model
+ * violates it, and fdtd_set_model checks it too.  The CPML grading keeps
+ * its single c_ref.  The adjoint is not provided for kr != (1, 1, 1)
+ * (fdtd_adjoint_step_n: EUNSUPPORTED).  A 2D run is ny = 1 with no y layer
+ * (the zero values beyond the grid make delta_y vanish there). */
+int fdtd_set_anisotropy(fdtd_ctx *ctx, const double kr[3]);
+
 /* Per-cell (sigma, kappa, alpha) for a layer of L equal cells on every face
  * (all six cpml_cells equal to L): ska_dev float [L][3], cell j = 0
  * outermost.  Converted to (b, a, 1/kappa) on the device.  Used by the
@@ -186,8 +199,8 @@ int fdtd_step_n(fdtd_ctx *ctx, int n);
  * [b, a, 1/kappa][node]) receives += dJ/d(profile) and needs cpml_grad at
  * create time (EINVAL otherwise).  Needs FP32 storage,
  * checkpoint_every > 0 and n equal to the current time index (ESTATE
- * otherwise), and a model without density (EUNSUPPORTED otherwise).  Leaves
- * the forward state undefined (call fdtd_reset). */
+ * otherwise), and an isotropic model without density (EUNSUPPORTED
+ * otherwise).  Leaves the forward state undefined (call fdtd_reset). */
 int fdtd_adjoint_step_n(fdtd_ctx *ctx, int n, const float *resid_dev,
                         float *grad_vel_dev, float *grad_cpml_dev);
 

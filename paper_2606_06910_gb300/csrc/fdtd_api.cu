@@ -382,6 +382,13 @@ double symbol_max()
     return std::max(best, s);
 }
 
+// c_max dt / h must not exceed 2 / (max_theta 2 sum_l a_l sin(l theta) * sqrt(sum_d kr_d))
+// (3 axes, kr = 1: 2 / (sqrt(3) ...) = 0.6672)
+double stability_limit(const fdtd_ctx *c)
+{
+    return 2.0 / (std::sqrt(c->kr[0] + c->kr[1] + c->kr[2]) * symbol_max());
+}
+
 bool fault_is(const char *what)
 {
     const char *f = getenv("FDTD_FAULT");
@@ -458,6 +465,8 @@ StepArgs base_args(const fdtd_ctx *c)
     a.dtr = (float)(c->d.dt * c->vscale);   // rho = 1
     a.nbr = c->var_rho ? c->nbr : nullptr;
     a.sscale = c->sscale;
+    for (int d = 0; d < 3; ++d)
+        a.kr[d] = (float)c->kr[d];
     a.inv_sscale = 1.f / c->sscale;
     a.src = c->nt_w > 0 ? c->src : nullptr;
     a.wavelet = c->wavelet;
@@ -699,6 +708,7 @@ int fdtd_create(const fdtd_desc *desc, void *workspace, size_t workspace_bytes, 
     c->es = L.es;
     c->tiles_x = L.tiles_x;
     c->tiles_y = L.tiles_y;
+    c->kr[0] = c->kr[1] = c->kr[2] = 1.0;
     c->vscale = 1.f;
     // FP16 keeps the whole state scaled by 2^10 (exact): small late-time
     // fields stay out of the FP16 subnormal range; the update is linear, so
@@ -802,7 +812,7 @@ int fdtd_set_model(fdtd_ctx *c, const float *vel, const float *rho)
     float vmin, vmax;
     memcpy(&vmin, &mm[0], 4);
     memcpy(&vmax, &mm[1], 4);
-    const double limit = 2.0 / (std::sqrt(3.0) * symbol_max());
+    const double limit = stability_limit(c);
     const double cfl = vmax * c->d.dt / c->d.h;
     if (cfl > limit)
         return fail(c, FDTD_EUNSTABLE, "c_max dt / h = %.6f exceeds the stability limit %.6f", cfl, limit);
@@ -838,6 +848,27 @@ int fdtd_set_cpml(fdtd_ctx *c, double R, double kappa_max, double alpha_frac, in
     CUDA_TRY(c, cudaMemcpyAsync(c->coef, coef.data(), coef.size() * 4, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->cpml_set = true;
+    return FDTD_OK;
+}
+
+int fdtd_set_anisotropy(fdtd_ctx *c, const double kr[3])
+{
+    if (!c || !kr)
+        return fail(c, FDTD_EINVAL, "NULL argument");
+    for (int d = 0; d < 3; ++d)
+        if (!(kr[d] > 0.0) || !std::isfinite(kr[d]))
+            return fail(c, FDTD_EINVAL, "anisotropy factors must be finite and positive");
+    const double old[3] = {c->kr[0], c->kr[1], c->kr[2]};
+    for (int d = 0; d < 3; ++d)
+        c->kr[d] = kr[d];
+    if (c->model_set) {
+        const double cfl = c->c_max * c->d.dt / c->d.h, limit = stability_limit(c);
+        if (cfl > limit) {
+            for (int d = 0; d < 3; ++d)
+                c->kr[d] = old[d];
+            return fail(c, FDTD_EUNSTABLE, "c_max dt / h = %.6f exceeds the anisotropic limit %.6f", cfl, limit);
+        }
+    }
     return FDTD_OK;
 }
 
@@ -1006,6 +1037,8 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
         return fail(c, FDTD_EINVAL, "grad_cpml needs cpml_grad at create time");
     if (c->var_rho)
         return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for constant density (rho = 1) only");
+    if (c->kr[0] != 1.0 || c->kr[1] != 1.0 || c->kr[2] != 1.0)
+        return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the isotropic system only");
     const bool want_prof = grad_cpml != nullptr;
     const int nmax = nmax_of(c->g);
     CUDA_TRY(c, cudaMemsetAsync(c->gradK, 0, (size_t)c->d.nshots * c->g.vol * 4, c->stream));

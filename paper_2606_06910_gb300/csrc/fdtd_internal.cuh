@@ -311,6 +311,7 @@ struct StepArgs {
     float dtr;                      // dt * vscale / rho (velocity update, constant density)
     const float *nbr;               // [vol] -dt * vscale / rho per node (variable density), or null
     float sscale, inv_sscale;       // stored state = sscale * physical state
+    float kr[3];                    // elliptic anisotropy: axis moduli kr_d K (x, y, z)
     const int *src;                 // [nshots][3] (z, y, x)
     const float *wavelet;           // [nshots][nt_w]
     int nt_w;
@@ -348,6 +349,7 @@ struct fdtd_ctx {
     float *kdt;             // -dt K / vscale per node [nz][ny][nxp] (0 in the row padding)
     float *nbr;             // -dt vscale / rho per node (variable density), same layout
     bool var_rho;           // fdtd_set_model was given a density
+    double kr[3];           // elliptic anisotropy factors (1, 1, 1: isotropic)
     float *coef;            // [3][3][nmax]: b, a, 1/kappa per axis and node
     float *wavelet;         // [nshots][nt_max]
     int nt_w;

@@ -309,6 +309,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
         C.cn[l] = make_float2(-A.c[l], -A.c[l]);
     }
     const float2 ndtr = make_float2(-A.dtr, -A.dtr);
+    const bool aniso = A.kr[0] != 1.f || A.kr[1] != 1.f || A.kr[2] != 1.f;   // CTA-uniform
 
     const long long fofs = (long long)shot * G.vol;
     const T *p_in = reinterpret_cast<const T *>(A.p_in) + fofs;
@@ -672,7 +673,10 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
             }
             // nkdt holds -dt K / vscale (zero beyond the grid)
             const V4 nkd = ldsf(reinterpret_cast<const float *>(S + L::OFF_K) + ty * TX + 4 * tx);
-            const V4 sb = add4(add4(hx4, hy4), hz4);
+            // elliptic anisotropy weights the axes (A.kr = 1, 1, 1 when isotropic)
+            const V4 sb = aniso ? add4(add4(mul4(splat4(A.kr[0]), hx4), mul4(splat4(A.kr[1]), hy4)),
+                                       mul4(splat4(A.kr[2]), hz4))
+                                : add4(add4(hx4, hy4), hz4);
             V4 pn = V4{fma2(nkd.a, sb.a, pt.a), fma2(nkd.b, sb.b, pt.b)};
             if (src_here && t == sz) {
                 const int i = sx - gx;   // select, not a dynamic register index

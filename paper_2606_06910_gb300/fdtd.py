@@ -125,6 +125,12 @@ class Fdtd:
         self._check(self.lib.fdtd_set_cpml(self.ctx, float(R), float(kappa_max), float(alpha_frac),
                                            int(q), float(c_ref) if c_ref is not None else -1.0))
 
+    def set_anisotropy(self, kr):
+        """Elliptic anisotropy: axis moduli kr_d K for (x, y, z); the wave
+        speed along axis d is c sqrt(kr_d)."""
+        arr = (ctypes.c_double * 3)(*[float(v) for v in kr])
+        self._check(self.lib.fdtd_set_anisotropy(self.ctx, ctypes.cast(arr, ctypes.c_void_p)))
+
     def set_cpml_ska(self, ska: torch.Tensor):
         _need(ska, (self.cells[0], 3), self.device, "ska")
         self._check(self.lib.fdtd_set_cpml_ska(self.ctx, _ptr(ska)))
