@@ -48,6 +48,10 @@ typedef struct {
     const unsigned char *slab[3]; /* 1 where the node lies in a d-slab */
     const double *rho_n;      /* density per node [nz][ny][nx], or NULL: rho everywhere */
     double kr[3];             /* elliptic anisotropy: modulus along axis d = kr[d] K (1 = isotropic) */
+    int staggered;            /* 1: v_d at half nodes i + 1/2 along d (the Yee reading of Sec. 3.1) */
+    const double *bv[3];      /* staggered: CPML coefficients of the velocity nodes (half-node depth) */
+    const double *av[3];
+    const double *kinvv[3];
 } og_grid;
 
 /* density at node i (collocated with p and v, Sec. 3.1) */
@@ -89,6 +93,36 @@ static double og_deriv(const og_grid *g, const double *f, int axis, long z, long
     return s / g->h;
 }
 
+/* Staggered derivatives (radius 4, weights w = c_1..c_4 for the offsets
+ * 1/2, 3/2, 5/2, 7/2).  v_d[i] lives at i + 1/2 along d:
+ *   forward  (p -> v):  (1/h) sum_l c_l (f_{i+l} - f_{i+1-l})   at i + 1/2,
+ *   backward (v -> p):  (1/h) sum_l c_l (f_{i+l-1} - f_{i-l})   at i.
+ * With zero values beyond the grid the backward operator is minus the
+ * transpose of the forward one. */
+static double og_deriv_fwd(const og_grid *g, const double *f, int axis, long z, long y, long x)
+{
+    long dz = axis == 2, dy = axis == 1, dx = axis == 0;
+    double s = 0.0;
+    for (int l = 1; l <= 4; l++) {
+        double fp = og_at(g, f, z + l * dz, y + l * dy, x + l * dx);
+        double fm = og_at(g, f, z + (1 - l) * dz, y + (1 - l) * dy, x + (1 - l) * dx);
+        s += g->w[l - 1] * (fp - fm);
+    }
+    return s / g->h;
+}
+
+static double og_deriv_bwd(const og_grid *g, const double *f, int axis, long z, long y, long x)
+{
+    long dz = axis == 2, dy = axis == 1, dx = axis == 0;
+    double s = 0.0;
+    for (int l = 1; l <= 4; l++) {
+        double fp = og_at(g, f, z + (l - 1) * dz, y + (l - 1) * dy, x + (l - 1) * dx);
+        double fm = og_at(g, f, z - l * dz, y - l * dy, x - l * dx);
+        s += g->w[l - 1] * (fp - fm);
+    }
+    return s / g->h;
+}
+
 static long og_axis_index(int axis, long z, long y, long x)
 {
     return axis == 0 ? x : (axis == 1 ? y : z);
@@ -106,11 +140,14 @@ void og_velocity_stage(const og_grid *g, og_state *st)
             for (long x = 0; x < nx; x++) {
                 long i = (z * ny + y) * nx + x;
                 for (int d = 0; d < 3; d++) {
-                    double gd = og_deriv(g, st->p, d, z, y, x);
+                    double gd = g->staggered ? og_deriv_fwd(g, st->p, d, z, y, x) : og_deriv(g, st->p, d, z, y, x);
                     long k = og_axis_index(d, z, y, x);
                     if (g->slab[d][k]) {
-                        st->psiv[d][i] = g->b[d][k] * st->psiv[d][i] + g->a[d][k] * gd;
-                        gd = g->kinv[d][k] * gd + st->psiv[d][i];
+                        const double *b = g->staggered ? g->bv[d] : g->b[d];
+                        const double *a = g->staggered ? g->av[d] : g->a[d];
+                        const double *kinv = g->staggered ? g->kinvv[d] : g->kinv[d];
+                        st->psiv[d][i] = b[k] * st->psiv[d][i] + a[k] * gd;
+                        gd = kinv[k] * gd + st->psiv[d][i];
                     }
                     st->v[d][i] -= g->dt / og_rho(g, i) * gd;
                 }
@@ -131,7 +168,8 @@ void og_pressure_stage(const og_grid *g, og_state *st, double *s_out)
                 long i = (z * ny + y) * nx + x;
                 double s = 0.0;
                 for (int d = 0; d < 3; d++) {
-                    double hd = og_deriv(g, st->v[d], d, z, y, x);
+                    double hd = g->staggered ? og_deriv_bwd(g, st->v[d], d, z, y, x)
+                                             : og_deriv(g, st->v[d], d, z, y, x);
                     long k = og_axis_index(d, z, y, x);
                     if (g->slab[d][k]) {
                         st->psip[d][i] = g->b[d][k] * st->psip[d][i] + g->a[d][k] * hd;
@@ -218,6 +256,7 @@ static void og_deriv_transpose_acc(const og_grid *g, const double *y, int axis, 
  *   h_d  = D_d v_d' ; psip_d' = b psip_d + a h_d ; p' = p - dt K sum_d (kinv h_d + psip_d')
  * (CPML terms only inside the d-slab), is transposed assignment by assignment
  * in reverse order.  The source term is a constant and has no adjoint.
+ * Collocated form only (g->staggered must be 0).
  */
 void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
                      double *gradK, double *gprof, long nmax)

@@ -70,6 +70,19 @@ def second_derivative_weights(r: int):
 WEIGHTS = [float(x) for x in first_derivative_weights(4)]
 
 
+def staggered_weights(r: int = 4):
+    """c_1..c_r of the staggered first derivative (the Yee reading of Sec. 3.1):
+    (f(x + (l - 1/2) h) - f(x - (l - 1/2) h)) with the unique weights exact for
+    polynomials of degree <= 2r - 1.  For r = 4: 1225/1024, -245/3072, 49/5120,
+    -5/7168."""
+    offs = [Fraction(2 * k - 1, 2) for k in range(-r + 1, r + 1)]   # -7/2 .. 7/2
+    c = fd_weights(offs, 1)
+    return [c[r - 1 + l] for l in range(1, r + 1)]
+
+
+STAGGERED_WEIGHTS = [float(x) for x in staggered_weights(4)]
+
+
 # ----------------------------------------------------------------------------
 # CPML profiles (Sec. 3.2, Tab. 2)
 # ----------------------------------------------------------------------------
@@ -114,6 +127,12 @@ def axis_profile(n: int, L_lo: int, L_hi: int, h: float, dt: float, c_ref: float
     alpha = alpha_frac sigma_max (1 - rho); b, a from cpml_coefficients.
     Returns dict with slab (uint8), rho, sigma, kappa, alpha, b, a, kinv.
     Outside the slabs: slab = 0, kinv = 1, b = a = 0 (unused).
+
+    Also bv, av, kinvv: the same profile at the half nodes i + 1/2 where the
+    staggered (Yee) form keeps v (reading: the velocity memory variables use
+    the slab index set of p, with depth (L_lo - i - 1/2)/L_lo on the low face
+    and (i + 1/2 - (n - 1 - L_hi))/L_hi, clamped to 1, on the high face; the
+    half node just inside the high slab, depth 1/(2 L_hi), is left out).
     """
     rho = np.zeros(n)
     slab = np.zeros(n, dtype=np.uint8)
@@ -134,7 +153,19 @@ def axis_profile(n: int, L_lo: int, L_hi: int, h: float, dt: float, c_ref: float
     b = np.where(slab == 1, b, 0.0)
     a = np.where(slab == 1, a, 0.0)
     kinv = np.where(slab == 1, kinv, 1.0)
-    return dict(slab=slab, rho=rho, sigma=sigma, kappa=kappa, alpha=alpha, b=b, a=a, kinv=kinv)
+    rv = np.zeros(n)
+    for i in range(n):
+        if i < L_lo:
+            rv[i] = (L_lo - i - 0.5) / L_lo
+        elif i >= n - L_hi:
+            rv[i] = min(1.0, (i + 0.5 - (n - 1 - L_hi)) / L_hi)
+    bv, av, kinvv = cpml_coefficients(smax * rv ** q, 1.0 + (kappa_max - 1.0) * rv ** q,
+                                      alpha_frac * smax * (1.0 - rv), dt)
+    bv = np.where(slab == 1, bv, 0.0)
+    av = np.where(slab == 1, av, 0.0)
+    kinvv = np.where(slab == 1, kinvv, 1.0)
+    return dict(slab=slab, rho=rho, sigma=sigma, kappa=kappa, alpha=alpha, b=b, a=a, kinv=kinv,
+                rho_v=rv, bv=bv, av=av, kinvv=kinvv)
 
 
 def make_profiles(shape, L, h, dt, c_ref, R=1e-8, q=3, kappa_max=5.0, alpha_frac=0.05):
@@ -152,7 +183,7 @@ def no_cpml_profiles(shape):
     out = []
     for n in (nx, ny, nz):
         out.append(dict(slab=np.zeros(n, np.uint8), b=np.zeros(n), a=np.zeros(n),
-                        kinv=np.ones(n)))
+                        kinv=np.ones(n), bv=np.zeros(n), av=np.zeros(n), kinvv=np.ones(n)))
     return out
 
 
@@ -168,7 +199,8 @@ class _Grid(ctypes.Structure):
                 ("h", ctypes.c_double), ("dt", ctypes.c_double), ("rho", ctypes.c_double),
                 ("w", ctypes.c_double * 4), ("periodic", ctypes.c_int),
                 ("K", ctypes.c_void_p), ("b", _P3), ("a", _P3), ("kinv", _P3),
-                ("slab", _P3), ("rho_n", ctypes.c_void_p), ("kr", ctypes.c_double * 3)]
+                ("slab", _P3), ("rho_n", ctypes.c_void_p), ("kr", ctypes.c_double * 3),
+                ("staggered", ctypes.c_int), ("bv", _P3), ("av", _P3), ("kinvv", _P3)]
 
 
 class _State(ctypes.Structure):
@@ -235,12 +267,16 @@ class Grid:
     constant or an array [nz][ny][nx] of per-node values (variable density,
     collocated with p and v: the velocity update at a node uses dt / rho of
     that node).
+    staggered: the Yee reading of Sec. 3.1 (v_d at half nodes i + 1/2 along
+    d, forward differences p -> v and backward v -> p with the staggered
+    weights; the CPML of v uses the half-node profiles bv, av, kinvv).
     Reading (Sec. 3.1 "normalized form"): physical units with rho given
     (1 in every workload here), velocity update scaled by dt/rho, pressure
     update by dt K, and each coefficient multiplies the whole CPML bracket.
     """
 
-    def __init__(self, K, h, dt, profiles=None, rho=1.0, periodic=False, weights=None, kr=(1.0, 1.0, 1.0)):
+    def __init__(self, K, h, dt, profiles=None, rho=1.0, periodic=False, weights=None, kr=(1.0, 1.0, 1.0),
+                 staggered=False):
         self.K = np.ascontiguousarray(K, dtype=np.float64)
         self.shape = self.K.shape
         self.h, self.dt = float(h), float(dt)
@@ -252,7 +288,10 @@ class Grid:
             assert self.rho_n.shape == self.K.shape
         self.periodic = bool(periodic)
         self.kr = tuple(float(r) for r in kr)   # (x, y, z): axis moduli kr_d K
-        self.weights = list(WEIGHTS if weights is None else weights)
+        self.staggered = bool(staggered)
+        if weights is None:
+            weights = STAGGERED_WEIGHTS if self.staggered else WEIGHTS
+        self.weights = list(weights)
         if profiles is None:
             profiles = no_cpml_profiles(self.shape)
         self.profiles = []
@@ -261,7 +300,10 @@ class Grid:
                 slab=np.ascontiguousarray(pr["slab"], dtype=np.uint8),
                 b=np.ascontiguousarray(pr["b"], dtype=np.float64),
                 a=np.ascontiguousarray(pr["a"], dtype=np.float64),
-                kinv=np.ascontiguousarray(pr["kinv"], dtype=np.float64)))
+                kinv=np.ascontiguousarray(pr["kinv"], dtype=np.float64),
+                bv=np.ascontiguousarray(pr.get("bv", pr["b"]), dtype=np.float64),
+                av=np.ascontiguousarray(pr.get("av", pr["a"]), dtype=np.float64),
+                kinvv=np.ascontiguousarray(pr.get("kinvv", pr["kinv"]), dtype=np.float64)))
         self._cg = self._make_c()
 
     def _make_c(self):
@@ -278,6 +320,10 @@ class Grid:
             g.a[d] = _ptr(pr["a"])
             g.kinv[d] = _ptr(pr["kinv"])
             g.slab[d] = _ptr(pr["slab"])
+            g.bv[d] = _ptr(pr["bv"])
+            g.av[d] = _ptr(pr["av"])
+            g.kinvv[d] = _ptr(pr["kinvv"])
+        g.staggered = 1 if self.staggered else 0
         g.rho_n = _ptr(self.rho_n) if self.rho_n is not None else None
         for d in range(3):
             g.kr[d] = self.kr[d]
@@ -330,7 +376,9 @@ def adjoint_step(grid: Grid, fwd: State, adj: State, gradK=None, gprof=None):
     fwd: forward state at the start of the step.  adj: adjoint of the state at
     the end of the step (receiver residuals already added), replaced by the
     adjoint at the start.  gradK: [nz,ny,nx] accumulator of dJ/dK.
-    gprof: [3, 3, nmax] accumulator of dJ/d(b, a, kinv) per axis and node."""
+    gprof: [3, 3, nmax] accumulator of dJ/d(b, a, kinv) per axis and node.
+    The collocated form only (the staggered form has no transpose here)."""
+    assert not grid.staggered, "adjoint_step: collocated form only"
     nmax = max(grid.shape)
     fc = fwd._c()
     ac = adj._c()
@@ -526,26 +574,38 @@ def symbol(theta, weights=None):
     return 2.0 * sum(w[l] * np.sin((l + 1) * theta) for l in range(len(w)))
 
 
-def stability_limit(weights=None):
-    """Largest c dt / h for which the 3D collocated leapfrog is stable:
-    (c dt / 2h) sqrt(3) max D-hat <= 1."""
+def staggered_symbol(theta, weights=None):
+    """S-hat(theta) = 2 sum_l c_l sin((l - 1/2) theta): the staggered first
+    derivative maps sin(theta i) at the nodes to (S-hat/h) cos(theta (i + 1/2))
+    at the half nodes, and cos at the half nodes back to -(S-hat/h) sin."""
+    w = STAGGERED_WEIGHTS if weights is None else weights
+    return 2.0 * sum(w[l] * np.sin((l + 0.5) * theta) for l in range(len(w)))
+
+
+def stability_limit(weights=None, staggered=False):
+    """Largest c dt / h for which the 3D leapfrog is stable:
+    (c dt / 2h) sqrt(3) max D-hat <= 1 (collocated), S-hat in the staggered form."""
     th = np.linspace(0.0, np.pi, 400001)
-    return 2.0 / (math.sqrt(3.0) * float(np.max(symbol(th, weights))))
+    sym = staggered_symbol(th, weights) if staggered else symbol(th, weights)
+    return 2.0 / (math.sqrt(3.0) * float(np.max(sym)))
 
 
-def standing_wave_state(shape, m, h, dt, rho, weights=None):
+def standing_wave_state(shape, m, h, dt, rho, weights=None, staggered=False):
     """Initial (p^0, v^{-1/2}) on a periodic grid for which the leapfrog gives
     p^n = phi cos(omega_h n dt) exactly, phi = prod_d sin(theta_d i_d),
     theta_d = 2 pi m_d / n_d, with v^{-1/2} = (dt / (2 rho)) D phi written in
-    closed form through the symbol (D sin = (D-hat/h) cos)."""
+    closed form through the symbol (D sin = (D-hat/h) cos).  staggered: v_d
+    sits at i_d + 1/2, so its cosine is taken there and S-hat replaces D-hat."""
     nz, ny, nx = shape
     mz, my, mx = m
     th = [2 * np.pi * mx / nx, 2 * np.pi * my / ny, 2 * np.pi * mz / nz]
     ix, iy, iz = np.arange(nx), np.arange(ny), np.arange(nz)
     sx, sy, sz = np.sin(th[0] * ix), np.sin(th[1] * iy), np.sin(th[2] * iz)
-    cx, cy, cz = np.cos(th[0] * ix), np.cos(th[1] * iy), np.cos(th[2] * iz)
+    half = 0.5 if staggered else 0.0
+    cx, cy, cz = np.cos(th[0] * (ix + half)), np.cos(th[1] * (iy + half)), np.cos(th[2] * (iz + half))
     phi = sz[:, None, None] * sy[None, :, None] * sx[None, None, :]
-    Dh = [symbol(t, weights) / h for t in th]
+    sym = staggered_symbol if staggered else symbol
+    Dh = [sym(t, weights) / h for t in th]
     st = State(shape)
     st["p"] = phi
     st["vx"] = dt / (2 * rho) * Dh[0] * sz[:, None, None] * sy[None, :, None] * cx[None, None, :]
