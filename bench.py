@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--forms-only", action="store_true", help="measure only the forms (profiling runs)")
-    ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock,density,aniso2d",
+    ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock,density,aniso2d,staggered",
                     help="comma list of forms measured after the main line ('' for none)")
     return ap.parse_args()
 
@@ -376,6 +376,38 @@ def form_density(dev, nsteps=96, warm=8):
     return {"workload": f"layered512, density (c/1500)^0.25, {warm} + {nsteps} timed steps", "unit": UNIT, **out}
 
 
+def form_staggered(dev, nsteps=96, warm=8):
+    """The staggered (Yee) form on the 512^3 layered workload (20 CPML cells)
+    at CFL 0.4 (its limit is 0.4488), against the collocated form at the same
+    dt: Mpoints/s and the fraction of measured HBM bandwidth of each (the
+    same algorithmic bytes per step)."""
+    import torch
+    from paper_2606_06910_gb300 import synth
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    w = synth.preset("layered512")
+    dt = 0.4 * w.h / w.vmax
+    vel = torch.from_numpy(w.velocity()).to(dev)
+    npts = float(np.prod(w.shape))
+    bytes_launch = algorithmic_bytes(w.shape, w.cpml_cells, 4)
+    peak, _ = measured_peaks()
+    out = {}
+    for name in ("collocated", "staggered"):
+        sim = Fdtd(w.shape, w.h, dt, cpml_cells=w.cpml_cells, nt_max=w.nt, device=dev)
+        sim.set_staggered(name == "staggered")
+        sim.set_model(vel)
+        sim.set_cpml(R=w.R, c_ref=w.vmax)
+        sim.inject(w.sources(), torch.from_numpy(w.wavelet()).to(dev))
+        sim.step(warm)
+        sim.sync()
+        secs = _timed(sim.stream, lambda: sim.step(nsteps))
+        ach = bytes_launch * nsteps / secs / 1e9
+        out[name] = {"value": round(npts * nsteps / secs / 1e6, 1), "ms_per_step": round(secs / nsteps * 1e3, 4),
+                     "roofline_frac": round(ach / peak, 4)}
+        del sim
+        torch.cuda.empty_cache()
+    return {"workload": f"layered512 at CFL 0.4, {warm} + {nsteps} timed steps", "unit": UNIT, **out}
+
+
 def form_aniso2d(dev, nt=1000, every=50):
     """The paper's 2D anisotropic CPML demonstration (Sec. 5): sum p^2 inside
     the layer relative to its peak, with a 10-cell layer and with none."""
@@ -599,6 +631,8 @@ def main():
                     forms[f] = form_tblock(dev)
                 elif f == "density":
                     forms[f] = form_density(dev)
+                elif f == "staggered":
+                    forms[f] = form_staggered(dev)
                 elif f == "aniso2d":
                     forms[f] = form_aniso2d(dev)
             except Exception as e:  # report, keep the main line

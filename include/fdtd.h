@@ -153,6 +153,25 @@ int fdtd_set_cpml(fdtd_ctx *ctx, double R, double kappa_max, double alpha_frac,
  * (the zero values beyond the grid make delta_y vanish there). */
 int fdtd_set_anisotropy(fdtd_ctx *ctx, const double kr[3]);
 
+/* Staggered (Yee) form of the same system (Sec. 3.1 names both grids):
+ * on = 1 keeps p at the nodes and v_d[i] at the half node i + 1/2 along d,
+ * with the staggered radius-4 derivatives
+ *   v_d <- v_d - dt/rho [ (1/kappa) D+ p + psi_v ],  D+ f[i] = (1/h) sum_l c_l (f[i+l] - f[i+1-l]),
+ *   p   <- p - dt K sum_d kr_d [ (1/kappa) D- v_d + psi_p ],  D- f[i] = (1/h) sum_l c_l (f[i+l-1] - f[i-l]),
+ * c = (1225/1024, -245/3072, 49/5120, -5/7168), zero values beyond the grid
+ * (so D- = -D+^T).  The velocity memory variables keep the slab index set
+ * of p and the grading of fdtd_set_cpml at the half-node depth
+ * (lo - i - 1/2)/lo on a low face and min(1, (i + 1/2 - (n - 1 - hi))/hi) on
+ * a high face.  Every array keeps its layout; FDTD_VX etc. then hold the
+ * half-node values.  The stability limit becomes
+ * 2 / (sqrt(sum_d kr_d) 2 sum_l |c_l|) = 0.44884 for kr = 1.
+ * on = 0 restores the collocated default.  Chosen before the first step
+ * (ESTATE after it until fdtd_reset).  EUNSUPPORTED for 16-bit storage, with
+ * a density or with learned profiles (fdtd_set_cpml_ska), and the adjoint
+ * is not provided (fdtd_adjoint_step_n: EUNSUPPORTED).  EUNSTABLE (form
+ * unchanged) if a set model violates the limit; fdtd_set_model checks it. */
+int fdtd_set_staggered(fdtd_ctx *ctx, int on);
+
 /* Per-cell (sigma, kappa, alpha) for a layer of L equal cells on every face
  * (all six cpml_cells equal to L): ska_dev float [L][3], cell j = 0
  * outermost.  Converted to (b, a, 1/kappa) on the device.  Used by the

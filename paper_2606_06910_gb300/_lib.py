@@ -50,6 +50,7 @@ _SIGS = {
     "fdtd_set_cpml": (c_int, [c_void_p, c_double, c_double, c_double, c_int, c_double]),
     "fdtd_set_cpml_ska": (c_int, [c_void_p, c_void_p]),
     "fdtd_set_anisotropy": (c_int, [c_void_p, c_void_p]),
+    "fdtd_set_staggered": (c_int, [c_void_p, c_int]),
     "fdtd_inject": (c_int, [c_void_p, ctypes.POINTER(c_int), c_void_p, c_int]),
     "fdtd_record": (c_int, [c_void_p, ctypes.POINTER(c_int), c_int, c_void_p]),
     "fdtd_step_n": (c_int, [c_void_p, c_int]),

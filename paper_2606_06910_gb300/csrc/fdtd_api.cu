@@ -150,7 +150,7 @@ void make_layout(const fdtd_desc *d, Layout *L)
     }
     L->kdt = take((size_t)g.vol * 4);
     L->nbr = take((size_t)g.vol * 4);
-    L->coef = take((size_t)9 * nmax_of(g) * 4);
+    L->coef = take((size_t)18 * nmax_of(g) * 4);
     L->wav = take(S * d->nt_max * 4);
     L->src = take(S * 3 * 4);
     L->rec = take((size_t)std::max(d->nrec_max, 1) * 16);
@@ -316,8 +316,13 @@ void choose_zchunk(fdtd_ctx *c)
     }
 }
 
+// Per-node CPML coefficients of one axis (normalised depth (L - j)/L at cell
+// j of a face, j = 0 outermost).  half: the coefficients of the velocity
+// nodes i + 1/2 of the staggered form, over the same slab index set: depth
+// (lo - i - 1/2)/lo on the low face, (i + 1/2 - (n - 1 - hi))/hi, at most 1,
+// on the high face.
 void host_profile(int n, int lo, int hi, double h, double dt, double R, double kmax, double afrac, int q, double cref,
-                  float *b, float *a, float *kinv)
+                  bool half, float *b, float *a, float *kinv)
 {
     for (int i = 0; i < n; ++i) {
         int L = 0;
@@ -335,6 +340,10 @@ void host_profile(int n, int lo, int hi, double h, double dt, double R, double k
             kinv[i] = 1.f;
             continue;
         }
+        if (half)   // the velocity node i + 1/2 (staggered form)
+            rho = i < lo ? double(lo - i) - 0.5 : std::min(double(hi), double(i - (n - 1 - hi)) + 0.5);
+        if (half)
+            rho /= L;
         const double smax = -(q + 1) * cref * std::log(R) / (2.0 * L * h);
         const double rq = std::pow(rho, q);
         const double sigma = smax * rq;
@@ -383,10 +392,18 @@ double symbol_max()
 }
 
 // c_max dt / h must not exceed 2 / (max_theta 2 sum_l a_l sin(l theta) * sqrt(sum_d kr_d))
-// (3 axes, kr = 1: 2 / (sqrt(3) ...) = 0.6672)
+// (3 axes, kr = 1: 2 / (sqrt(3) ...) = 0.6672).  The staggered symbol
+// 2 sum_l c_l sin((l - 1/2) theta) peaks at theta = pi with 2 sum_l |c_l|
+// (3 axes: 0.44884).
 double stability_limit(const fdtd_ctx *c)
 {
-    return 2.0 / (std::sqrt(c->kr[0] + c->kr[1] + c->kr[2]) * symbol_max());
+    double smax = symbol_max();
+    if (c->staggered) {
+        smax = 0.0;
+        for (int l = 0; l < 4; ++l)
+            smax += 2.0 * std::fabs(kStagWeights[l]);
+    }
+    return 2.0 / (std::sqrt(c->kr[0] + c->kr[1] + c->kr[2]) * smax);
 }
 
 bool fault_is(const char *what)
@@ -458,10 +475,14 @@ StepArgs base_args(const fdtd_ctx *c)
         a.cb[d] = c->coef + (d * 3 + 0) * nmax;
         a.ca[d] = c->coef + (d * 3 + 1) * nmax;
         a.ck[d] = c->coef + (d * 3 + 2) * nmax;
+        const int hv = c->staggered ? 9 : 0;
+        a.cbv[d] = c->coef + (hv + d * 3 + 0) * nmax;
+        a.cav[d] = c->coef + (hv + d * 3 + 1) * nmax;
+        a.ckv[d] = c->coef + (hv + d * 3 + 2) * nmax;
         a.psip[d] = c->psip[d];
     }
     for (int l = 0; l < 4; ++l)
-        a.c[l] = (float)(kWeights[l] / c->d.h);
+        a.c[l] = (float)((c->staggered ? kStagWeights[l] : kWeights[l]) / c->d.h);
     a.dtr = (float)(c->d.dt * c->vscale);   // rho = 1
     a.nbr = c->var_rho ? c->nbr : nullptr;
     a.sscale = c->sscale;
@@ -766,8 +787,8 @@ int fdtd_create(const fdtd_desc *desc, void *workspace, size_t workspace_bytes, 
     choose_zchunk(c);
     // coefficient table: no CPML anywhere until set_cpml (b = a = 0, 1/kappa = 1)
     const int nmax = nmax_of(c->g);
-    std::vector<float> coef((size_t)9 * nmax, 0.f);
-    for (int d = 0; d < 3; ++d)
+    std::vector<float> coef((size_t)18 * nmax, 0.f);
+    for (int d = 0; d < 6; ++d)
         for (int i = 0; i < nmax; ++i)
             coef[(d * 3 + 2) * nmax + i] = 1.f;
     cudaError_t e = cudaMemcpyAsync(c->coef, coef.data(), coef.size() * 4, cudaMemcpyHostToDevice, c->stream);
@@ -801,6 +822,8 @@ int fdtd_set_model(fdtd_ctx *c, const float *vel, const float *rho)
 {
     if (!c || !vel)
         return fail(c, FDTD_EINVAL, "vel is NULL");
+    if (rho && c->staggered)
+        return fail(c, FDTD_EUNSUPPORTED, "the staggered form is provided for constant density only");
     unsigned mm[3];
     c->vscale = 1.f;
     c->model_set = false;
@@ -840,14 +863,18 @@ int fdtd_set_cpml(fdtd_ctx *c, double R, double kappa_max, double alpha_frac, in
         c_ref = c->c_max;
     }
     const int nmax = nmax_of(c->g);
-    std::vector<float> coef((size_t)9 * nmax, 0.f);
+    std::vector<float> coef((size_t)18 * nmax, 0.f);
     const int n[3] = {c->g.nx, c->g.ny, c->g.nz};
-    for (int d = 0; d < 3; ++d)
-        host_profile(n[d], c->g.lo[d], c->g.hi[d], c->d.h, c->d.dt, R, kappa_max, alpha_frac, q, c_ref,
-                     &coef[(d * 3 + 0) * nmax], &coef[(d * 3 + 1) * nmax], &coef[(d * 3 + 2) * nmax]);
+    for (int hv = 0; hv < 2; ++hv)
+        for (int d = 0; d < 3; ++d) {
+            float *t = &coef[(size_t)(9 * hv + d * 3) * nmax];
+            host_profile(n[d], c->g.lo[d], c->g.hi[d], c->d.h, c->d.dt, R, kappa_max, alpha_frac, q, c_ref,
+                         hv == 1, t, t + nmax, t + 2 * nmax);
+        }
     CUDA_TRY(c, cudaMemcpyAsync(c->coef, coef.data(), coef.size() * 4, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->cpml_set = true;
+    c->cpml_ska = false;
     return FDTD_OK;
 }
 
@@ -872,6 +899,32 @@ int fdtd_set_anisotropy(fdtd_ctx *c, const double kr[3])
     return FDTD_OK;
 }
 
+int fdtd_set_staggered(fdtd_ctx *c, int on)
+{
+    if (!c)
+        return FDTD_EINVAL;
+    if (on != 0 && on != 1)
+        return fail(c, FDTD_EINVAL, "on must be 0 or 1");
+    if (c->t != 0)
+        return fail(c, FDTD_ESTATE, "the form is chosen before the first step (or after fdtd_reset)");
+    if (on && c->d.storage != FDTD_F32)
+        return fail(c, FDTD_EUNSUPPORTED, "the staggered form is provided for FP32 storage only");
+    if (on && c->var_rho)
+        return fail(c, FDTD_EUNSUPPORTED, "the staggered form is provided for constant density only");
+    if (on && c->cpml_ska)
+        return fail(c, FDTD_EUNSUPPORTED, "learned profiles are provided for the collocated form only");
+    const bool old = c->staggered;
+    c->staggered = on != 0;
+    if (c->model_set) {
+        const double cfl = c->c_max * c->d.dt / c->d.h, limit = stability_limit(c);
+        if (cfl > limit) {
+            c->staggered = old;
+            return fail(c, FDTD_EUNSTABLE, "c_max dt / h = %.6f exceeds the limit %.6f of the form", cfl, limit);
+        }
+    }
+    return FDTD_OK;
+}
+
 int fdtd_set_cpml_ska(fdtd_ctx *c, const float *ska)
 {
     if (!c || !ska)
@@ -882,8 +935,11 @@ int fdtd_set_cpml_ska(fdtd_ctx *c, const float *ska)
             return fail(c, FDTD_EINVAL, "learned profiles need equal CPML cells on all faces");
     if (L < 1 || L > 64)
         return fail(c, FDTD_EINVAL, "learned layer must have 1..64 cells");
+    if (c->staggered)
+        return fail(c, FDTD_EUNSUPPORTED, "learned profiles are provided for the collocated form only");
     CUDA_TRY(c, launch_ska_to_coef(c, ska, L));
     c->cpml_set = true;
+    c->cpml_ska = true;
     return FDTD_OK;
 }
 
@@ -1039,6 +1095,8 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
         return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for constant density (rho = 1) only");
     if (c->kr[0] != 1.0 || c->kr[1] != 1.0 || c->kr[2] != 1.0)
         return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the isotropic system only");
+    if (c->staggered)
+        return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the collocated form only");
     const bool want_prof = grad_cpml != nullptr;
     const int nmax = nmax_of(c->g);
     CUDA_TRY(c, cudaMemsetAsync(c->gradK, 0, (size_t)c->d.nshots * c->g.vol * 4, c->stream));

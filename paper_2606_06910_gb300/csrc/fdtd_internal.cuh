@@ -24,6 +24,10 @@ constexpr int NSTAGE = 3;                 // TMA pipeline depth (planes in fligh
 // polynomials up to degree 8 exactly.
 constexpr double kWeights[4] = {4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0};
 
+// Weights c_1..c_4 of the staggered radius-4 first derivative (the Yee form of
+// Sec. 3.1: offsets 1/2, 3/2, 5/2, 7/2), exact for polynomials up to degree 7.
+constexpr double kStagWeights[4] = {1225.0 / 1024.0, -245.0 / 3072.0, 49.0 / 5120.0, -5.0 / 7168.0};
+
 // device error word bits
 constexpr unsigned ERR_TIMEOUT = 1u;
 constexpr unsigned ERR_NONFINITE = 2u;
@@ -307,6 +311,7 @@ struct StepArgs {
     void *psiv_out[3];
     void *psip[3];                  // updated in place
     const float *cb[3], *ca[3], *ck[3];   // b, a, 1/kappa per node of each axis
+    const float *cbv[3], *cav[3], *ckv[3];   // the same for the velocity update (half nodes when staggered)
     float c[4];                     // a_l / h
     float dtr;                      // dt * vscale / rho (velocity update, constant density)
     const float *nbr;               // [vol] -dt * vscale / rho per node (variable density), or null
@@ -350,7 +355,8 @@ struct fdtd_ctx {
     float *nbr;             // -dt vscale / rho per node (variable density), same layout
     bool var_rho;           // fdtd_set_model was given a density
     double kr[3];           // elliptic anisotropy factors (1, 1, 1: isotropic)
-    float *coef;            // [3][3][nmax]: b, a, 1/kappa per axis and node
+    bool staggered;         // the staggered (Yee) form: v_d at half nodes
+    float *coef;            // [2][3][3][nmax]: b, a, 1/kappa per axis and node, then at the half nodes
     float *wavelet;         // [nshots][nt_max]
     int nt_w;
     int *src;               // [nshots][3]

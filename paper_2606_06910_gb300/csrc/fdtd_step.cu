@@ -170,6 +170,61 @@ __device__ __forceinline__ float2 dx2(float2 P0, float2 P1, float2 P2, float2 P3
     return r;
 }
 
+// Staggered (Yee) form: v_d[i] lives at i + 1/2.  With c_l / h in C:
+//   forward  (p -> v at i):  sum_l c_l (f[i + l] - f[i + 1 - l])
+//   backward (v -> p at i):  sum_l c_l (f[i + l - 1] - f[i - l])
+// For a pair of outputs one of the two terms of each l falls on an aligned
+// pair (packed FMA) and the other does not (two scalar FMAs).
+// Forward derivative of the pair at offsets 4, 5 of P0..P4 (offsets 0..9).
+__device__ __forceinline__ float2 sdf2(float2 P0, float2 P1, float2 P2, float2 P3, float2 P4, const Coef &C)
+{
+    float2 r = mul2(C.cp[1], P3);       // l = 2: f(+2), f(+3)
+    r = fma2(C.cp[3], P4, r);           // l = 4: f(+4), f(+5)
+    r = fma2(C.cn[0], P2, r);           // l = 1: f(0), f(1)
+    r = fma2(C.cn[2], P1, r);           // l = 3: f(-2), f(-1)
+    const float c1 = C.cp[0].x, c3 = C.cp[2].x, m2 = C.cn[1].x, m4 = C.cn[3].x;
+    r.x = fmaf(c1, P2.y, r.x);          // l = 1: f(+1)
+    r.y = fmaf(c1, P3.x, r.y);
+    r.x = fmaf(m2, P1.y, r.x);          // l = 2: f(-1)
+    r.y = fmaf(m2, P2.x, r.y);
+    r.x = fmaf(c3, P3.y, r.x);          // l = 3: f(+3)
+    r.y = fmaf(c3, P4.x, r.y);
+    r.x = fmaf(m4, P0.y, r.x);          // l = 4: f(-3)
+    r.y = fmaf(m4, P1.x, r.y);
+    return r;
+}
+
+// forward derivative of 4 outputs from offsets -4..7 (u, v, w as in dx4);
+// each pair takes the operation order of sdf2, so halo pairs match
+__device__ __forceinline__ V4 sdf4(const V4 &u, const V4 &v, const V4 &w, const Coef &C)
+{
+    return V4{sdf2(u.a, u.b, v.a, v.b, w.a, C), sdf2(u.b, v.a, v.b, w.a, w.b, C)};
+}
+
+// backward derivative of the pair at offsets 4, 5 of P0..P4 (offsets 0..9)
+__device__ __forceinline__ float2 sdb2(float2 P0, float2 P1, float2 P2, float2 P3, float2 P4, const Coef &C)
+{
+    float2 r = mul2(C.cp[0], P2);       // l = 1: f(0), f(1)
+    r = fma2(C.cp[2], P3, r);           // l = 3: f(+2), f(+3)
+    r = fma2(C.cn[1], P1, r);           // l = 2: f(-2), f(-1)
+    r = fma2(C.cn[3], P0, r);           // l = 4: f(-4), f(-3)
+    const float c2 = C.cp[1].x, c4 = C.cp[3].x, m1 = C.cn[0].x, m3 = C.cn[2].x;
+    r.x = fmaf(m1, P1.y, r.x);          // l = 1: f(-1)
+    r.y = fmaf(m1, P2.x, r.y);
+    r.x = fmaf(c2, P2.y, r.x);          // l = 2: f(+1)
+    r.y = fmaf(c2, P3.x, r.y);
+    r.x = fmaf(m3, P0.y, r.x);          // l = 3: f(-3)
+    r.y = fmaf(m3, P1.x, r.y);
+    r.x = fmaf(c4, P3.y, r.x);          // l = 4: f(+3)
+    r.y = fmaf(c4, P4.x, r.y);
+    return r;
+}
+
+__device__ __forceinline__ V4 sdb4(const V4 &u, const V4 &v, const V4 &w, const Coef &C)
+{
+    return V4{sdb2(u.a, u.b, v.a, v.b, w.a, C), sdb2(u.b, v.a, v.b, w.a, w.b, C)};
+}
+
 __device__ __forceinline__ void cpml2(float2 &g, float2 psi, float2 b, float2 a, float2 k)
 {
     const float2 pn = fma2(b, psi, mul2(a, g));
@@ -228,15 +283,16 @@ __device__ __forceinline__ void tape4(float *tape, long long idx, int off, const
 
 // Queue work of one plane.  Logical entry j of each 9-deep queue lives in
 // slot j: pq[j] = p(t + j), vzq[j] = v'_z(t - 4 + j); the queues shift by one
-// slot per plane.
-template <typename Zvel>
+// slot per plane.  kStag: v_z[t + 4] sits at t + 4.5 and the pressure at t
+// reads v_z at t - 4 .. t + 3 (the staggered neighbour sets).
+template <bool kStag, typename Zvel>
 __device__ __forceinline__ void zblock(V4 (&pq)[9], V4 (&vzq)[9], const V4 &pnew, const Coef &C, Zvel &&zvel,
                                        V4 &pt, V4 &hz)
 {
     pq[8] = pnew;
     V4 gz;
     {
-        const V4 m[4] = {pq[3], pq[2], pq[1], pq[0]};
+        const V4 m[4] = {pq[kStag ? 4 : 3], pq[kStag ? 3 : 2], pq[kStag ? 2 : 1], pq[kStag ? 1 : 0]};
         const V4 p[4] = {pq[5], pq[6], pq[7], pq[8]};
         gz = dnb(m, p, C);
     }
@@ -244,7 +300,7 @@ __device__ __forceinline__ void zblock(V4 (&pq)[9], V4 (&vzq)[9], const V4 &pnew
     vzq[8] = zvel(gz);
     {
         const V4 m[4] = {vzq[3], vzq[2], vzq[1], vzq[0]};
-        const V4 p[4] = {vzq[5], vzq[6], vzq[7], vzq[8]};
+        const V4 p[4] = {vzq[kStag ? 4 : 5], vzq[kStag ? 5 : 6], vzq[kStag ? 6 : 7], vzq[kStag ? 7 : 8]};
         hz = dnb(m, p, C);
     }
 #pragma unroll
@@ -281,12 +337,15 @@ __host__ __device__ __forceinline__ int chunk_count(const StepArgs &A)
 // with its 4-node x / y halo and its z range with 4 planes either side lie
 // inside the grid and outside every CPML slab, so it needs no memory
 // variables, no coefficient tables and no masks at the grid edge.  The same
-// arithmetic in the same order runs in both forms.
-template <typename T, bool kEdge, bool kRho>
+// arithmetic in the same order runs in both forms.  kStag selects the
+// staggered (Yee) neighbour sets; the velocity CPML then reads the half-node
+// coefficients sCxv, sCyv, A.cbv.. (the node tables otherwise).
+template <typename T, bool kEdge, bool kRho, bool kStag>
 __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorMap &mPq, const CUtensorMap &mVX,
                                           const CUtensorMap &mVY, const CUtensorMap &mVZ, const CUtensorMap &mK,
                                           const StepArgs &A, int z0, int z1, unsigned char *smem,
-                                          float (*sCx)[TX + 8], float (*sCy)[TY + 8])
+                                          float (*sCx)[TX + 8], float (*sCy)[TY + 8],
+                                          float (*sCxv)[TX + 8], float (*sCyv)[TY + 8])
 {
     using L = StageLayout<T>;
     float *svx = reinterpret_cast<float *>(smem + NSTAGE * L::BYTES);
@@ -337,6 +396,16 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
         const int c = i / (TY + 8), y = y0 - 4 + i % (TY + 8);
         const bool in = y >= 0 && y < G.ny && in_slab(y, G.ny, G.lo[1], G.hi[1]);
         sCy[c][i % (TY + 8)] = in ? (c == 0 ? A.cb[1][y] : (c == 1 ? A.ca[1][y] : A.ck[1][y])) : (c == 2 ? 1.f : 0.f);
+    }
+    for (int i = tid; kStag && kEdge && i < 3 * (TX + 8); i += NTHREADS) {
+        const int c = i / (TX + 8), x = x0 - 4 + i % (TX + 8);
+        const bool in = x >= 0 && x < G.nx && in_slab(x, G.nx, G.lo[0], G.hi[0]);
+        sCxv[c][i % (TX + 8)] = in ? (c == 0 ? A.cbv[0][x] : (c == 1 ? A.cav[0][x] : A.ckv[0][x])) : (c == 2 ? 1.f : 0.f);
+    }
+    for (int i = tid; kStag && kEdge && i < 3 * (TY + 8); i += NTHREADS) {
+        const int c = i / (TY + 8), y = y0 - 4 + i % (TY + 8);
+        const bool in = y >= 0 && y < G.ny && in_slab(y, G.ny, G.lo[1], G.hi[1]);
+        sCyv[c][i % (TY + 8)] = in ? (c == 0 ? A.cbv[1][y] : (c == 1 ? A.cav[1][y] : A.ckv[1][y])) : (c == 2 ? 1.f : 0.f);
     }
 
     // validity of the 4 own nodes (ghost nodes beyond the grid hold 0)
@@ -510,8 +579,8 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                 if (zs_v) {
                     const long long izv = slab_index(G, 2, zv, gy, gx);
                     const V4 psvz = ldg_v4(psiv_in[2] + izv);
-                    const V4 b = splat4(__ldg(A.cb[2] + zv)), a = splat4(__ldg(A.ca[2] + zv)),
-                             k = splat4(__ldg(A.ck[2] + zv));
+                    const V4 b = splat4(__ldg(A.cbv[2] + zv)), a = splat4(__ldg(A.cav[2] + zv)),
+                             k = splat4(__ldg(A.ckv[2] + zv));
                     if (owned && stape[2])
                         tape4(stape[2], izv, 0, gz, psvz);
                     const V4 pn = cpml4(gz, psvz, b, a, k);
@@ -528,7 +597,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
             return vzn;
         };
         V4 pt, hz4;
-        zblock(pq, vzq, pnew, C, zvel, pt, hz4);
+        zblock<kStag>(pq, vzq, pnew, C, zvel, pt, hz4);
 
         if (ok && active) {
             const unsigned char *Sp = S + L::OFF_P;   // p plane, origin (x0 - 8, y0 - 8)
@@ -536,14 +605,15 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
             // ---- v'_x, own nodes
             {
                 const int lrow = (ty + 8) * L::PW, lx = 4 * tx + 8;
-                V4 g = dx4(lds<T>(Sp, lrow + lx - 4), lds<T>(Sp, lrow + lx), lds<T>(Sp, lrow + lx + 4), C);
+                const V4 u = lds<T>(Sp, lrow + lx - 4), v = lds<T>(Sp, lrow + lx), w = lds<T>(Sp, lrow + lx + 4);
+                V4 g = kStag ? sdf4(u, v, w, C) : dx4(u, v, w, C);
                 if (own_x) {
                     const int cx = 4 * tx + 4;
                     const long long ix = slab_index(G, 0, t, gy, gx);
                     const V4 psvx = ldg_v4(psiv_in[0] + ix);
                     if (stape[0])
                         tape4(stape[0], ix, 0, g, psvx);
-                    const V4 pn = cpml4(g, psvx, ldsf(&sCx[0][cx]), ldsf(&sCx[1][cx]), ldsf(&sCx[2][cx]));
+                    const V4 pn = cpml4(g, psvx, ldsf(&sCxv[0][cx]), ldsf(&sCxv[1][cx]), ldsf(&sCxv[2][cx]));
                     st_out(psiv_out[0] + ix, to_f4(pn));
                 }
                 V4 vn = kRho ? fmav(nbo, g, lds<T>(S + L::OFF_VX, ty * L::VXW + 4 * tx + 8))
@@ -560,7 +630,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                 V4 m[4], p[4];
 #pragma unroll
                 for (int l = 1; l <= 4; ++l) {
-                    m[l - 1] = lds<T>(Sp, (ly - l) * L::PW + lx);
+                    m[l - 1] = lds<T>(Sp, (ly - l + (kStag ? 1 : 0)) * L::PW + lx);
                     p[l - 1] = lds<T>(Sp, (ly + l) * L::PW + lx);
                 }
                 V4 g = dnb(m, p, C);
@@ -569,7 +639,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     const V4 psvy = ldg_v4(psiv_in[1] + iy);
                     if (stape[1])
                         tape4(stape[1], iy, 0, g, psvy);
-                    const V4 pn = cpml4(g, psvy, splat4(sCy[0][ty + 4]), splat4(sCy[1][ty + 4]), splat4(sCy[2][ty + 4]));
+                    const V4 pn = cpml4(g, psvy, splat4(sCyv[0][ty + 4]), splat4(sCyv[1][ty + 4]), splat4(sCyv[2][ty + 4]));
                     st_out(psiv_out[1] + iy, to_f4(pn));
                 }
                 V4 vn = kRho ? fmav(nbo, g, lds<T>(S + L::OFF_VY, (ty + 4) * TX + 4 * tx))
@@ -586,15 +656,15 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                 float2 m[4], p[4];
 #pragma unroll
                 for (int l = 1; l <= 4; ++l) {
-                    m[l - 1] = lds2<T>(Sp, (ly - l) * L::PW + lx);
+                    m[l - 1] = lds2<T>(Sp, (ly - l + (kStag ? 1 : 0)) * L::PW + lx);
                     p[l - 1] = lds2<T>(Sp, (ly + l) * L::PW + lx);
                 }
                 float2 g = dnb2(m, p, C);
                 const int r = yh_y - y0 + 4;
                 if (halo_psi_y) {
                     const float2 psh = Io<T>::ld2(psiv_in[1] + slab_index(G, 1, t, yh_y, yh_x));
-                    cpml2(g, psh, make_float2(sCy[0][r], sCy[0][r]), make_float2(sCy[1][r], sCy[1][r]),
-                          make_float2(sCy[2][r], sCy[2][r]));
+                    cpml2(g, psh, make_float2(sCyv[0][r], sCyv[0][r]), make_float2(sCyv[1][r], sCyv[1][r]),
+                          make_float2(sCyv[2][r], sCyv[2][r]));
                 }
                 float2 vn = fma2(kRho ? nbh : ndtr, g, lds2<T>(S + L::OFF_VY, r * TX + (yh_x - x0)));
                 if (kEdge) {
@@ -604,13 +674,14 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                 *reinterpret_cast<float2 *>(svy + r * TX + (yh_x - x0)) = vn;
             } else {
                 const int lrow = (xh_y - y0 + 8) * L::PW, lx = xh_x - x0 + 8;
-                float2 g = dx2(lds2<T>(Sp, lrow + lx - 4), lds2<T>(Sp, lrow + lx - 2), lds2<T>(Sp, lrow + lx),
-                               lds2<T>(Sp, lrow + lx + 2), lds2<T>(Sp, lrow + lx + 4), C);
+                const float2 P0 = lds2<T>(Sp, lrow + lx - 4), P1 = lds2<T>(Sp, lrow + lx - 2), P2 = lds2<T>(Sp, lrow + lx),
+                             P3 = lds2<T>(Sp, lrow + lx + 2), P4 = lds2<T>(Sp, lrow + lx + 4);
+                float2 g = kStag ? sdf2(P0, P1, P2, P3, P4, C) : dx2(P0, P1, P2, P3, P4, C);
                 const int cx = xh_x - x0 + 4;
                 if (halo_psi_x) {
                     const float2 psh = Io<T>::ld2(psiv_in[0] + slab_index(G, 0, t, xh_y, xh_x));
-                    cpml2(g, psh, *reinterpret_cast<const float2 *>(&sCx[0][cx]),
-                          *reinterpret_cast<const float2 *>(&sCx[1][cx]), *reinterpret_cast<const float2 *>(&sCx[2][cx]));
+                    cpml2(g, psh, *reinterpret_cast<const float2 *>(&sCxv[0][cx]),
+                          *reinterpret_cast<const float2 *>(&sCxv[1][cx]), *reinterpret_cast<const float2 *>(&sCxv[2][cx]));
                 }
                 float2 vn = fma2(kRho ? nbh : ndtr, g, lds2<T>(S + L::OFF_VX, (xh_y - y0) * L::VXW + lx));
                 if (kEdge) {
@@ -634,14 +705,15 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
         if (active) {
             // ---- pressure step at plane t
             const float *sxr = svx + ty * L::SVXW + 4 * tx;
-            V4 hx4 = dx4(ldsf(sxr), ldsf(sxr + 4), ldsf(sxr + 8), C);
+            V4 hx4 = kStag ? sdb4(ldsf(sxr), ldsf(sxr + 4), ldsf(sxr + 8), C)
+                           : dx4(ldsf(sxr), ldsf(sxr + 4), ldsf(sxr + 8), C);
             V4 hy4;
             {
                 V4 m[4], p[4];
 #pragma unroll
                 for (int l = 1; l <= 4; ++l) {
                     m[l - 1] = ldsf(svy + (ty + 4 - l) * TX + 4 * tx);
-                    p[l - 1] = ldsf(svy + (ty + 4 + l) * TX + 4 * tx);
+                    p[l - 1] = ldsf(svy + (ty + 4 + l - (kStag ? 1 : 0)) * TX + 4 * tx);
                 }
                 hy4 = dnb(m, p, C);
             }
@@ -717,7 +789,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
     }
 }
 
-template <typename T, bool kRho>
+template <typename T, bool kRho, bool kStag>
 __global__ void __launch_bounds__(NTHREADS, kMinBlocks)
     fdtd_step_kernel(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mPq,
                      const __grid_constant__ CUtensorMap mVX, const __grid_constant__ CUtensorMap mVY,
@@ -729,6 +801,11 @@ __global__ void __launch_bounds__(NTHREADS, kMinBlocks)
     // and y range [y0-4, y0+TY+4); 0, 0, 1 outside the slabs and the grid
     __shared__ __align__(16) float sCx[3][TX + 8];
     __shared__ __align__(16) float sCy[3][TY + 8];
+    // the staggered form's velocity coefficients (half-node depths)
+    __shared__ __align__(16) float sCxv[kStag ? 3 : 1][TX + 8];
+    __shared__ __align__(16) float sCyv[kStag ? 3 : 1][TY + 8];
+    float (*vx)[TX + 8] = kStag ? sCxv : sCx;
+    float (*vy)[TY + 8] = kStag ? sCyv : sCy;
     const Geom &G = A.g;
     const int x0 = (blockIdx.x % A.tiles_x) * TX, y0 = (blockIdx.x / A.tiles_x) * TY;
     int z0, z1;
@@ -736,34 +813,38 @@ __global__ void __launch_bounds__(NTHREADS, kMinBlocks)
     const bool interior = x0 - 4 >= G.lo[0] && x0 + TX + 4 <= G.nx - G.hi[0] && y0 - 4 >= G.lo[1] &&
                           y0 + TY + 4 <= G.ny - G.hi[1] && z0 - 4 >= G.lo[2] && z1 + 4 <= G.nz - G.hi[2];
     if (interior)
-        step_body<T, false, kRho>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy);
+        step_body<T, false, kRho, kStag>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy, vx, vy);
     else
-        step_body<T, true, kRho>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy);
+        step_body<T, true, kRho, kStag>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy, vx, vy);
 }
 
-template <typename T, bool kRho>
+template <typename T, bool kRho, bool kStag>
 static cudaError_t launch_step_tr(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream)
 {
     using L = StageLayout<T>;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(fdtd_step_kernel<T, kRho>,
+        cudaError_t e = cudaFuncSetAttribute(fdtd_step_kernel<T, kRho, kStag>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
         if (e != cudaSuccess)
             return e;
         attr_done = true;
     }
     dim3 grid(c->tiles_x * c->tiles_y, chunk_count(a), c->d.nshots);
-    fdtd_step_kernel<T, kRho><<<grid, NTHREADS, L::SMEM, stream>>>(
+    fdtd_step_kernel<T, kRho, kStag><<<grid, NTHREADS, L::SMEM, stream>>>(
         c->maps[set][0], c->maps[set][1], c->maps[set][2], c->maps[set][3], c->maps[set][4], c->mapK, a);
     return cudaGetLastError();
 }
 
-// a.nbr selects the variable-density form
+// a.nbr selects the variable-density form, c->staggered the staggered one
+// (FP32 storage and constant density only; the API enforces both)
 template <typename T>
 static cudaError_t launch_step_t(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream)
 {
-    return a.nbr ? launch_step_tr<T, true>(c, a, set, stream) : launch_step_tr<T, false>(c, a, set, stream);
+    if constexpr (std::is_same<T, float>::value)
+        if (c->staggered)
+            return a.nbr ? cudaErrorInvalidValue : launch_step_tr<T, false, true>(c, a, set, stream);
+    return a.nbr ? launch_step_tr<T, true, false>(c, a, set, stream) : launch_step_tr<T, false, false>(c, a, set, stream);
 }
 
 // One step over z in [a.zbase, a.zend) on `stream`; `set` is the ping-pong
@@ -784,8 +865,8 @@ template <typename T>
 static int occupancy_t(int *blocks)
 {
     using L = StageLayout<T>;
-    cudaFuncSetAttribute(fdtd_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fdtd_step_kernel<T, false>, NTHREADS, L::SMEM) ==
+    cudaFuncSetAttribute(fdtd_step_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fdtd_step_kernel<T, false, false>, NTHREADS, L::SMEM) ==
                    cudaSuccess
                ? 0
                : -1;

@@ -131,6 +131,11 @@ class Fdtd:
         arr = (ctypes.c_double * 3)(*[float(v) for v in kr])
         self._check(self.lib.fdtd_set_anisotropy(self.ctx, ctypes.cast(arr, ctypes.c_void_p)))
 
+    def set_staggered(self, on: bool = True):
+        """Staggered (Yee) form: v_d at the half nodes i + 1/2, staggered
+        radius-4 derivatives; FP32 storage, constant density, forward only."""
+        self._check(self.lib.fdtd_set_staggered(self.ctx, 1 if on else 0))
+
     def set_cpml_ska(self, ska: torch.Tensor):
         _need(ska, (self.cells[0], 3), self.device, "ska")
         self._check(self.lib.fdtd_set_cpml_ska(self.ctx, _ptr(ska)))
