@@ -22,6 +22,12 @@
  *     update (psi_{p,d});
  *   - outside every slab nothing of the CPML is touched (Sec. 3.2: sigma = 0,
  *     kappa = 1, psi = 0 reduce to the interior update).
+ * Two options of the same system:
+ *   - staggered (the Yee reading of Sec. 3.1): v_d at half nodes i + 1/2,
+ *     forward differences p -> v and backward v -> p with the staggered
+ *     weights, and the velocity CPML at half-node depths;
+ *   - local CPML grading: b_d, a_d per node (bn, an), for a sigma_max taken
+ *     from the velocity at the node instead of one reference velocity.
  * Grid values beyond the outermost node are zero (or wrap, in periodic mode,
  * which the energy and dispersion tests use).
  *
@@ -52,7 +58,20 @@ typedef struct {
     const double *bv[3];      /* staggered: CPML coefficients of the velocity nodes (half-node depth) */
     const double *av[3];
     const double *kinvv[3];
+    const double *bn[3];      /* local grading: b_d per node [nz][ny][nx] (NULL: the 1D b[d]) */
+    const double *an[3];      /* local grading: a_d per node (NULL: the 1D a[d]) */
 } og_grid;
+
+/* CPML coefficients of axis d at node i (axis index k) */
+static double og_b(const og_grid *g, int d, long i, long k)
+{
+    return g->bn[d] ? g->bn[d][i] : g->b[d][k];
+}
+
+static double og_a(const og_grid *g, int d, long i, long k)
+{
+    return g->an[d] ? g->an[d][i] : g->a[d][k];
+}
 
 /* density at node i (collocated with p and v, Sec. 3.1) */
 static double og_rho(const og_grid *g, long i)
@@ -143,10 +162,10 @@ void og_velocity_stage(const og_grid *g, og_state *st)
                     double gd = g->staggered ? og_deriv_fwd(g, st->p, d, z, y, x) : og_deriv(g, st->p, d, z, y, x);
                     long k = og_axis_index(d, z, y, x);
                     if (g->slab[d][k]) {
-                        const double *b = g->staggered ? g->bv[d] : g->b[d];
-                        const double *a = g->staggered ? g->av[d] : g->a[d];
                         const double *kinv = g->staggered ? g->kinvv[d] : g->kinv[d];
-                        st->psiv[d][i] = b[k] * st->psiv[d][i] + a[k] * gd;
+                        const double b = g->staggered ? g->bv[d][k] : og_b(g, d, i, k);
+                        const double a = g->staggered ? g->av[d][k] : og_a(g, d, i, k);
+                        st->psiv[d][i] = b * st->psiv[d][i] + a * gd;
                         gd = kinv[k] * gd + st->psiv[d][i];
                     }
                     st->v[d][i] -= g->dt / og_rho(g, i) * gd;
@@ -172,7 +191,7 @@ void og_pressure_stage(const og_grid *g, og_state *st, double *s_out)
                                              : og_deriv(g, st->v[d], d, z, y, x);
                     long k = og_axis_index(d, z, y, x);
                     if (g->slab[d][k]) {
-                        st->psip[d][i] = g->b[d][k] * st->psip[d][i] + g->a[d][k] * hd;
+                        st->psip[d][i] = og_b(g, d, i, k) * st->psip[d][i] + og_a(g, d, i, k) * hd;
                         hd = g->kinv[d][k] * hd + st->psip[d][i];
                     }
                     s += g->kr[d] * hd;
@@ -256,7 +275,7 @@ static void og_deriv_transpose_acc(const og_grid *g, const double *y, int axis, 
  *   h_d  = D_d v_d' ; psip_d' = b psip_d + a h_d ; p' = p - dt K sum_d (kinv h_d + psip_d')
  * (CPML terms only inside the d-slab), is transposed assignment by assignment
  * in reverse order.  The source term is a constant and has no adjoint.
- * Collocated form only (g->staggered must be 0).
+ * Collocated form with 1D profiles only (g->staggered = 0, bn = an = NULL).
  */
 void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
                      double *gradK, double *gprof, long nmax)

@@ -177,6 +177,39 @@ def make_profiles(shape, L, h, dt, c_ref, R=1e-8, q=3, kappa_max=5.0, alpha_frac
             for d in range(3)]
 
 
+def local_profiles(vel, L, h, dt, R=1e-8, q=3, kappa_max=5.0, alpha_frac=0.05):
+    """Local-velocity grading (the heterogeneous-media extension named in
+    Sec. 7): at every node of a d-slab, sigma_max takes the velocity c of
+    that node in place of the one reference velocity, so sigma = sigma_max(c)
+    rho_d^q and alpha = alpha_frac sigma_max(c) (1 - rho_d), with the node's
+    normalised depth rho_d along d; kappa does not depend on c.
+    Returns [x, y, z] dicts with b, a, sigma as [nz][ny][nx] arrays (0
+    outside the d-slabs); 1/kappa stays the 1D profile of make_profiles."""
+    vel = np.asarray(vel, dtype=np.float64)
+    nz, ny, nx = vel.shape
+    ns = (nx, ny, nz)
+    out = []
+    for d in range(3):
+        lo, hi = L[2 * d], L[2 * d + 1]
+        pr = axis_profile(ns[d], lo, hi, h, dt, 1.0, R, q, kappa_max, alpha_frac)
+        shp = [1, 1, 1]
+        shp[2 - d] = ns[d]
+        depth = pr["rho"].reshape(shp)
+        slab = pr["slab"].reshape(shp).astype(bool)
+        Lnode = np.where(np.arange(ns[d]) < lo, lo, hi).reshape(shp)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            smax = np.where(slab, -(q + 1) * vel * math.log(R) / (2.0 * np.maximum(Lnode, 1) * h), 0.0)
+        sigma = smax * depth ** q
+        kappa = 1.0 + (kappa_max - 1.0) * depth ** q
+        alpha = alpha_frac * smax * (1.0 - depth)
+        b, a, _ = cpml_coefficients(sigma, np.broadcast_to(kappa, vel.shape), alpha, dt)
+        slab3 = np.broadcast_to(slab, vel.shape)
+        out.append(dict(b=np.ascontiguousarray(np.where(slab3, b, 0.0)),
+                        a=np.ascontiguousarray(np.where(slab3, a, 0.0)),
+                        sigma=np.ascontiguousarray(np.where(slab3, sigma, 0.0))))
+    return out
+
+
 def no_cpml_profiles(shape):
     """Profiles with no slab anywhere (plain interior update everywhere)."""
     nz, ny, nx = shape
@@ -200,7 +233,8 @@ class _Grid(ctypes.Structure):
                 ("w", ctypes.c_double * 4), ("periodic", ctypes.c_int),
                 ("K", ctypes.c_void_p), ("b", _P3), ("a", _P3), ("kinv", _P3),
                 ("slab", _P3), ("rho_n", ctypes.c_void_p), ("kr", ctypes.c_double * 3),
-                ("staggered", ctypes.c_int), ("bv", _P3), ("av", _P3), ("kinvv", _P3)]
+                ("staggered", ctypes.c_int), ("bv", _P3), ("av", _P3), ("kinvv", _P3),
+                ("bn", _P3), ("an", _P3)]
 
 
 class _State(ctypes.Structure):
@@ -267,6 +301,8 @@ class Grid:
     constant or an array [nz][ny][nx] of per-node values (variable density,
     collocated with p and v: the velocity update at a node uses dt / rho of
     that node).
+    local: per-node (b, a) of each axis from local_profiles (local-velocity
+    grading; the 1D slab flags and 1/kappa still come from profiles).
     staggered: the Yee reading of Sec. 3.1 (v_d at half nodes i + 1/2 along
     d, forward differences p -> v and backward v -> p with the staggered
     weights; the CPML of v uses the half-node profiles bv, av, kinvv).
@@ -276,7 +312,7 @@ class Grid:
     """
 
     def __init__(self, K, h, dt, profiles=None, rho=1.0, periodic=False, weights=None, kr=(1.0, 1.0, 1.0),
-                 staggered=False):
+                 staggered=False, local=None):
         self.K = np.ascontiguousarray(K, dtype=np.float64)
         self.shape = self.K.shape
         self.h, self.dt = float(h), float(dt)
@@ -289,6 +325,13 @@ class Grid:
         self.periodic = bool(periodic)
         self.kr = tuple(float(r) for r in kr)   # (x, y, z): axis moduli kr_d K
         self.staggered = bool(staggered)
+        self.local = None
+        if local is not None:
+            assert not self.staggered, "local grading: collocated form only"
+            self.local = [dict(b=np.ascontiguousarray(lp["b"], dtype=np.float64),
+                               a=np.ascontiguousarray(lp["a"], dtype=np.float64)) for lp in local]
+            for lp in self.local:
+                assert lp["b"].shape == self.shape and lp["a"].shape == self.shape
         if weights is None:
             weights = STAGGERED_WEIGHTS if self.staggered else WEIGHTS
         self.weights = list(weights)
@@ -324,6 +367,9 @@ class Grid:
             g.av[d] = _ptr(pr["av"])
             g.kinvv[d] = _ptr(pr["kinvv"])
         g.staggered = 1 if self.staggered else 0
+        for d in range(3):
+            g.bn[d] = _ptr(self.local[d]["b"]) if self.local is not None else None
+            g.an[d] = _ptr(self.local[d]["a"]) if self.local is not None else None
         g.rho_n = _ptr(self.rho_n) if self.rho_n is not None else None
         for d in range(3):
             g.kr[d] = self.kr[d]
@@ -378,7 +424,7 @@ def adjoint_step(grid: Grid, fwd: State, adj: State, gradK=None, gprof=None):
     adjoint at the start.  gradK: [nz,ny,nx] accumulator of dJ/dK.
     gprof: [3, 3, nmax] accumulator of dJ/d(b, a, kinv) per axis and node.
     The collocated form only (the staggered form has no transpose here)."""
-    assert not grid.staggered, "adjoint_step: collocated form only"
+    assert not grid.staggered and grid.local is None, "adjoint_step: collocated form, 1D profiles"
     nmax = max(grid.shape)
     fc = fwd._c()
     ac = adj._c()

@@ -1,0 +1,160 @@
+"""Pins of the oracle's local-velocity CPML grading (heterogeneous media, the
+extension Sec. 7 names): at a node of a d-slab sigma_max uses the velocity of
+that node, sigma_max(c) = -(q+1) c ln(R) / (2 L h), so the layer's
+continuous normal-incidence round trip exp(-2 int sigma / c ds) is R for
+every column whatever its velocity.  The checks: the reduction to the 1D
+grading for a homogeneous model (bit for bit), the round trip per column on
+unequal faces, the monotone shape of the coefficients, and absorption with
+long-time stability in a strongly layered model.  CPU only."""
+import math
+
+import numpy as np
+
+from oracle import oracle as O
+from paper_2606_06910_gb300 import synth
+
+
+def test_homogeneous_model_reduces_to_the_1d_grading_bitwise():
+    shape, cells, h, c = (18, 20, 22), (3, 4, 2, 5, 4, 3), 10.0, 2300.0
+    dt = 0.5 * h / c
+    vel = np.full(shape, c)
+    prof = O.make_profiles(shape, cells, h, dt, c, R=1e-6)
+    lp = O.local_profiles(vel, cells, h, dt, R=1e-6)
+    for d in range(3):
+        shp = [1, 1, 1]
+        shp[2 - d] = shape[2 - d]
+        assert np.array_equal(lp[d]["b"], np.broadcast_to(prof[d]["b"].reshape(shp), shape)), d
+        assert np.array_equal(lp[d]["a"], np.broadcast_to(prof[d]["a"].reshape(shp), shape)), d
+    rng = np.random.default_rng(4)
+    out = []
+    for local in (None, lp):
+        st = O.State(shape)
+        st["p"] = rng.standard_normal(shape) if not out else out[0][1]
+        init = st["p"].copy()
+        O.run(O.Grid(vel ** 2, h, dt, prof, local=local), st, 6)
+        out.append((st, init))
+    for k in O.FIELDS:
+        assert np.array_equal(out[0][0][k], out[1][0][k]), k
+
+
+def test_round_trip_is_R_for_every_column():
+    """The outermost node of each face has normalised depth 1, so sigma there
+    is sigma_max(c) and -2 sigma_max(c) L h / ((q + 1) c) must equal ln R for
+    the face's own L and the node's own c (unequal faces, random velocities)."""
+    rng = np.random.default_rng(8)
+    shape, cells, h, R, q = (14, 15, 16), (3, 5, 2, 4, 6, 2), 7.5, 1e-7, 3
+    vel = rng.uniform(1400.0, 5200.0, size=shape)
+    lp = O.local_profiles(vel, cells, h, 1e-3, R=R, q=q)
+    nz, ny, nx = shape
+    faces = [(0, (slice(None), slice(None), 0), cells[0]), (0, (slice(None), slice(None), nx - 1), cells[1]),
+             (1, (slice(None), 0, slice(None)), cells[2]), (1, (slice(None), ny - 1, slice(None)), cells[3]),
+             (2, (0, slice(None), slice(None)), cells[4]), (2, (nz - 1, slice(None), slice(None)), cells[5])]
+    for d, sl, L in faces:
+        s = lp[d]["sigma"][sl]
+        c = vel[sl]
+        lnR = -2.0 * s * L * h / ((q + 1) * c)
+        assert np.allclose(lnR, math.log(R), rtol=1e-12, atol=0), (d, L)
+
+
+def test_local_coefficients_shape():
+    """b in (0, 1], a <= 0 inside the slabs, zero outside; along a column
+    into a face (velocity constant along it) b falls towards the outside; at
+    equal depth a faster node is damped harder."""
+    shape, cells, h = (24, 6, 30), (8, 8, 0, 0, 6, 6), 10.0
+    dt = 1e-3
+    vel = synth.layered_model(shape, seed=3, vmin=1500.0, vmax=4500.0, amp_cells=1.0).astype(np.float64)
+    vel = np.repeat(vel[:, :, :1], shape[2], axis=2)     # layers constant along x
+    lp = O.local_profiles(vel, cells, h, dt, R=1e-8)
+    b, a = lp[0]["b"], lp[0]["a"]
+    inx = np.zeros(shape[2], bool)
+    inx[:8] = inx[-8:] = True
+    assert np.all((b[:, :, inx] > 0) & (b[:, :, inx] <= 1) & (a[:, :, inx] <= 0))
+    assert np.all(b[:, :, ~inx] == 0) and np.all(a[:, :, ~inx] == 0)
+    assert np.all(np.diff(b[:, :, :8], axis=2) > 0)        # less damping going inwards
+    z_slow, z_fast = int(np.argmin(vel[:, 0, 0])), int(np.argmax(vel[:, 0, 0]))
+    assert b[z_fast, 0, 0] < b[z_slow, 0, 0]
+
+
+def test_layered_model_absorbs_and_stays_stable():
+    """A 2D section (ny = 1) of a 1500-4500 m/s layered model with 10-cell
+    layers on the x and z faces graded from the local velocity: the field
+    energy falls below 1e-3 of its peak and stays bounded over a long run."""
+    nz, nx, h, L = 90, 90, 10.0, 10
+    shape, cells = (nz, 1, nx), (L, L, 0, 0, L, L)
+    vel = synth.layered_model(shape, seed=6, vmin=1500.0, vmax=4500.0, amp_cells=2.0).astype(np.float64)
+    dt = 0.5 * h / vel.max()
+    prof = O.make_profiles(shape, cells, h, dt, vel.max(), R=1e-5)
+    g = O.Grid(vel ** 2, h, dt, prof, local=O.local_profiles(vel, cells, h, dt, R=1e-5))
+    st = O.State(shape)
+    nt = 3000
+    wav = synth.ricker(nt, dt, 12.0)
+    e = []
+    for k in range(nt // 50):
+        O.run(g, st, 50, 50 * k, (45, 0, 45), wav)
+        e.append(float(np.sum(st["p"][L:-L, :, L:-L] ** 2)))
+    e = np.array(e)
+    assert e[-1] < 1e-3 * e.max(), e[-1] / e.max()
+    assert np.all(np.isfinite(e)) and e[-10:].max() < 2e-3 * e.max()
+
+
+def test_each_node_uses_its_own_coefficients():
+    """One velocity stage from psi = 0 leaves psi_v,d = a_d(node) delta_d p,
+    with delta_d p read off a run without a layer; a second stage with p = 0
+    (no new derivative) multiplies psi_v,d by b_d(node).  Random velocities
+    make every node's pair different, so a coefficient taken from another
+    node or axis shows."""
+    rng = np.random.default_rng(12)
+    shape, cells, h = (12, 13, 14), (3, 4, 2, 3, 4, 2), 10.0
+    vel = rng.uniform(1500.0, 4000.0, size=shape)
+    dt = 0.5 * h / vel.max()
+    prof = O.make_profiles(shape, cells, h, dt, vel.max(), R=1e-6)
+    lp = O.local_profiles(vel, cells, h, dt, R=1e-6)
+    p0 = rng.standard_normal(shape)
+    free = O.State(shape)
+    free["p"] = p0
+    O.velocity_stage(O.Grid(vel ** 2, h, dt), free)
+    st = O.State(shape)
+    st["p"] = p0
+    g = O.Grid(vel ** 2, h, dt, prof, local=lp)
+    O.velocity_stage(g, st)
+    nz, ny, nx = shape
+    for d, ax in enumerate("xyz"):
+        delta = -free["v" + ax] / dt
+        n = (nx, ny, nz)[d]
+        shp = [1, 1, 1]
+        shp[2 - d] = n
+        slab = np.broadcast_to(prof[d]["slab"].reshape(shp).astype(bool), shape)
+        expect = np.where(slab, lp[d]["a"] * delta, 0.0)
+        assert np.max(np.abs(st["psiv_" + ax] - expect)) <= 1e-12 * np.max(np.abs(expect)), ax
+    psi1 = {ax: st["psiv_" + ax].copy() for ax in "xyz"}
+    st["p"] = np.zeros(shape)
+    O.velocity_stage(g, st)
+    for d, ax in enumerate("xyz"):
+        assert np.max(np.abs(st["psiv_" + ax] - lp[d]["b"] * psi1[ax])) <= 1e-14 * np.max(np.abs(psi1[ax])), ax
+
+
+def test_pressure_stage_uses_each_nodes_coefficients():
+    """The same check for psi_p: with v only along axis d the pressure
+    bracket of a run without a layer is delta_d v_d, and one pressure stage
+    from psi = 0 leaves psi_p,d = a_d(node) delta_d v_d."""
+    rng = np.random.default_rng(13)
+    shape, cells, h = (12, 13, 14), (3, 4, 2, 3, 4, 2), 10.0
+    vel = rng.uniform(1500.0, 4000.0, size=shape)
+    dt = 0.5 * h / vel.max()
+    prof = O.make_profiles(shape, cells, h, dt, vel.max(), R=1e-6)
+    lp = O.local_profiles(vel, cells, h, dt, R=1e-6)
+    nz, ny, nx = shape
+    for d, ax in enumerate("xyz"):
+        v0 = rng.standard_normal(shape)
+        free = O.State(shape)
+        free["v" + ax] = v0
+        delta = O.pressure_stage(O.Grid(vel ** 2, h, dt), free, want_bracket=True)
+        st = O.State(shape)
+        st["v" + ax] = v0
+        O.pressure_stage(O.Grid(vel ** 2, h, dt, prof, local=lp), st)
+        n = (nx, ny, nz)[d]
+        shp = [1, 1, 1]
+        shp[2 - d] = n
+        slab = np.broadcast_to(prof[d]["slab"].reshape(shp).astype(bool), shape)
+        expect = np.where(slab, lp[d]["a"] * delta, 0.0)
+        assert np.max(np.abs(st["psip_" + ax] - expect)) <= 1e-12 * np.max(np.abs(expect)), ax
