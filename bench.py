@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--forms-only", action="store_true", help="measure only the forms (profiling runs)")
-    ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock,density,aniso2d,staggered",
+    ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock,density,aniso2d,staggered,local_cpml",
                     help="comma list of forms measured after the main line ('' for none)")
     return ap.parse_args()
 
@@ -408,6 +408,35 @@ def form_staggered(dev, nsteps=96, warm=8):
     return {"workload": f"layered512 at CFL 0.4, {warm} + {nsteps} timed steps", "unit": UNIT, **out}
 
 
+def form_local_cpml(dev, nsteps=96, warm=8):
+    """Local-velocity CPML grading on the 512^3 layered workload (20 cells):
+    b, a per slab node from the node's velocity, against the 1D grading with
+    c_ref = c_max; Mpoints/s of both.  The per-node tables add 8 B per slab
+    node and axis read per step."""
+    import torch
+    from paper_2606_06910_gb300 import synth
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    w = synth.preset("layered512")
+    vel = torch.from_numpy(w.velocity()).to(dev)
+    npts = float(np.prod(w.shape))
+    out = {}
+    for name in ("1d", "local"):
+        sim = Fdtd(w.shape, w.h, w.dt, cpml_cells=w.cpml_cells, nt_max=w.nt, cpml_local=name == "local", device=dev)
+        sim.set_model(vel)
+        if name == "local":
+            sim.set_cpml_local(vel, R=w.R)
+        else:
+            sim.set_cpml(R=w.R, c_ref=w.vmax)
+        sim.inject(w.sources(), torch.from_numpy(w.wavelet()).to(dev))
+        sim.step(warm)
+        sim.sync()
+        secs = _timed(sim.stream, lambda: sim.step(nsteps))
+        out[name] = {"value": round(npts * nsteps / secs / 1e6, 1), "ms_per_step": round(secs / nsteps * 1e3, 4)}
+        del sim
+        torch.cuda.empty_cache()
+    return {"workload": f"layered512, {warm} + {nsteps} timed steps", "unit": UNIT, **out}
+
+
 def form_aniso2d(dev, nt=1000, every=50):
     """The paper's 2D anisotropic CPML demonstration (Sec. 5): sum p^2 inside
     the layer relative to its peak, with a 10-cell layer and with none."""
@@ -633,6 +662,8 @@ def main():
                     forms[f] = form_density(dev)
                 elif f == "staggered":
                     forms[f] = form_staggered(dev)
+                elif f == "local_cpml":
+                    forms[f] = form_local_cpml(dev)
                 elif f == "aniso2d":
                     forms[f] = form_aniso2d(dev)
             except Exception as e:  # report, keep the main line

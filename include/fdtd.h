@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define FDTD_ABI_VERSION 1
+#define FDTD_ABI_VERSION 2
 
 typedef struct fdtd_ctx fdtd_ctx;
 
@@ -88,6 +88,7 @@ typedef struct {
     int nrec_max;            /* receiver capacity */
     int checkpoint_every;    /* > 0: keep checkpoints every C steps (adjoint) */
     int cpml_grad;           /* != 0: also keep what dJ/d(CPML profile) needs */
+    int cpml_local;          /* != 0: reserve per-node CPML coefficients (fdtd_set_cpml_local) */
     void *stream;            /* cudaStream_t to enqueue on; NULL = default */
 } fdtd_desc;
 
@@ -139,6 +140,26 @@ int fdtd_set_model(fdtd_ctx *ctx, const float *vel_dev, const float *rho_dev);
  * EINVAL for R outside (0, 1], kappa_max < 1, alpha_frac < 0 or q < 0. */
 int fdtd_set_cpml(fdtd_ctx *ctx, double R, double kappa_max, double alpha_frac,
                   int q, double c_ref);
+
+/* Local-velocity CPML grading (heterogeneous media, the extension Sec. 7
+ * names): at every node of the d-slab, sigma_max takes the velocity of that
+ * node in place of one reference velocity,
+ *   sigma_max(c) = -(q+1) c ln(R) / (2 L h),  sigma = sigma_max rho^q,
+ *   alpha = alpha_frac sigma_max(c) (1 - rho),  kappa = 1 + (kappa_max - 1) rho^q,
+ * with the node's normalised depth rho along d and the face's own L, so the
+ * continuous round trip is R for every column.  b, a are computed per slab
+ * node on the device in double and stored as float (8 B per slab node and
+ * axis, shared by the shots, read by every step); 1/kappa stays per axis.
+ * vel_dev: float [nz][ny][nx] in m/s, read during the call (normally the
+ * model given to fdtd_set_model).  Requires cpml_local at create time
+ * (ESTATE otherwise) and fdtd_set_model first (ESTATE).  Replaces any
+ * previous grading; fdtd_set_cpml or fdtd_set_cpml_ska replace it in turn.
+ * EINVAL for parameters as in fdtd_set_cpml or a slab velocity that is not
+ * finite and positive; EUNSUPPORTED with 16-bit storage or the staggered
+ * form, and the adjoint is not provided (fdtd_adjoint_step_n: EUNSUPPORTED).
+ * Synchronises. */
+int fdtd_set_cpml_local(fdtd_ctx *ctx, const float *vel_dev, double R, double kappa_max,
+                        double alpha_frac, int q);
 
 /* Elliptic anisotropy (the acoustic system of the paper's 2D CPML
  * demonstration, Sec. 5): the pressure update becomes

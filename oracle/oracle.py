@@ -177,26 +177,32 @@ def make_profiles(shape, L, h, dt, c_ref, R=1e-8, q=3, kappa_max=5.0, alpha_frac
             for d in range(3)]
 
 
-def local_profiles(vel, L, h, dt, R=1e-8, q=3, kappa_max=5.0, alpha_frac=0.05):
+def local_profiles(vel, L, h, dt, R=1e-8, q=3, kappa_max=5.0, alpha_frac=0.05, full_shape=None, origin=(0, 0, 0)):
     """Local-velocity grading (the heterogeneous-media extension named in
     Sec. 7): at every node of a d-slab, sigma_max takes the velocity c of
     that node in place of the one reference velocity, so sigma = sigma_max(c)
     rho_d^q and alpha = alpha_frac sigma_max(c) (1 - rho_d), with the node's
     normalised depth rho_d along d; kappa does not depend on c.
     Returns [x, y, z] dicts with b, a, sigma as [nz][ny][nx] arrays (0
-    outside the d-slabs); 1/kappa stays the 1D profile of make_profiles."""
+    outside the d-slabs); 1/kappa stays the 1D profile of make_profiles.
+    full_shape / origin: vel is the box of a larger grid starting at origin
+    (z, y, x); depths then follow the larger grid's faces."""
     vel = np.asarray(vel, dtype=np.float64)
     nz, ny, nx = vel.shape
     ns = (nx, ny, nz)
+    fz, fy, fx = vel.shape if full_shape is None else full_shape
+    fns = (fx, fy, fz)
+    org = (origin[2], origin[1], origin[0])
     out = []
     for d in range(3):
         lo, hi = L[2 * d], L[2 * d + 1]
-        pr = axis_profile(ns[d], lo, hi, h, dt, 1.0, R, q, kappa_max, alpha_frac)
+        pr = axis_profile(fns[d], lo, hi, h, dt, 1.0, R, q, kappa_max, alpha_frac)
+        sl = slice(org[d], org[d] + ns[d])
         shp = [1, 1, 1]
         shp[2 - d] = ns[d]
-        depth = pr["rho"].reshape(shp)
-        slab = pr["slab"].reshape(shp).astype(bool)
-        Lnode = np.where(np.arange(ns[d]) < lo, lo, hi).reshape(shp)
+        depth = pr["rho"][sl].reshape(shp)
+        slab = pr["slab"][sl].reshape(shp).astype(bool)
+        Lnode = np.where(np.arange(fns[d]) < lo, lo, hi)[sl].reshape(shp)
         with np.errstate(divide="ignore", invalid="ignore"):
             smax = np.where(slab, -(q + 1) * vel * math.log(R) / (2.0 * np.maximum(Lnode, 1) * h), 0.0)
         sigma = smax * depth ** q

@@ -36,7 +36,7 @@ class Desc(ctypes.Structure):
     _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("nshots", c_int),
                 ("h", c_double), ("dt", c_double), ("cpml_cells", c_int * 6),
                 ("storage", c_int), ("tblock_k", c_int), ("nt_max", c_int), ("nrec_max", c_int),
-                ("checkpoint_every", c_int), ("cpml_grad", c_int), ("stream", c_void_p)]
+                ("checkpoint_every", c_int), ("cpml_grad", c_int), ("cpml_local", c_int), ("stream", c_void_p)]
 
 
 _SIGS = {
@@ -51,6 +51,7 @@ _SIGS = {
     "fdtd_set_cpml_ska": (c_int, [c_void_p, c_void_p]),
     "fdtd_set_anisotropy": (c_int, [c_void_p, c_void_p]),
     "fdtd_set_staggered": (c_int, [c_void_p, c_int]),
+    "fdtd_set_cpml_local": (c_int, [c_void_p, c_void_p, c_double, c_double, c_double, c_int]),
     "fdtd_inject": (c_int, [c_void_p, ctypes.POINTER(c_int), c_void_p, c_int]),
     "fdtd_record": (c_int, [c_void_p, ctypes.POINTER(c_int), c_int, c_void_p]),
     "fdtd_step_n": (c_int, [c_void_p, c_int]),
@@ -89,7 +90,7 @@ def load() -> ctypes.CDLL:
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            if lib.fdtd_abi_version() != 1:
+            if lib.fdtd_abi_version() != 2:
                 raise RuntimeError("libfdtd ABI version mismatch")
             _lib = lib
         return _lib

@@ -22,6 +22,7 @@ cudaError_t launch_field(const fdtd_ctx *c, bool get, void *internal, float *den
 cudaError_t launch_energy(const fdtd_ctx *c, const void *p, const int *box);
 cudaError_t launch_misfit(const fdtd_ctx *c, const float *dobs, int nt, float *resid);
 cudaError_t launch_ska_to_coef(const fdtd_ctx *c, const float *ska, int L);
+cudaError_t launch_local_coef(const fdtd_ctx *c, const float *vel, double R, double kmax, double afrac, int q);
 cudaError_t launch_ska_backward(const fdtd_ctx *c, const float *ska, const float *gprof, int L, float *gska);
 cudaError_t launch_mlp_forward(const float *th, const float *X, int n, float ssc, float asc, float *out, float *act,
                                cudaStream_t s);
@@ -69,6 +70,7 @@ struct Layout {
     size_t kdt, nbr, coef, wav, src, rec, rec_off, err, red, minmax;
     int ncp;
     size_t ckpt, ckpt_slot, tape_s, tape_slab[3], ap[2], av[3][2], apsiv[3][2], apsip[3][2], gradK, gprof;
+    size_t lcoef[3][2];
     size_t total;
 };
 
@@ -151,6 +153,9 @@ void make_layout(const fdtd_desc *d, Layout *L)
     L->kdt = take((size_t)g.vol * 4);
     L->nbr = take((size_t)g.vol * 4);
     L->coef = take((size_t)18 * nmax_of(g) * 4);
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 2; ++k)
+            L->lcoef[a][k] = d->cpml_local ? take((size_t)g.slab[a] * 4) : 0;
     L->wav = take(S * d->nt_max * 4);
     L->src = take(S * 3 * 4);
     L->rec = take((size_t)std::max(d->nrec_max, 1) * 16);
@@ -483,6 +488,10 @@ StepArgs base_args(const fdtd_ctx *c)
     }
     for (int l = 0; l < 4; ++l)
         a.c[l] = (float)((c->staggered ? kStagWeights[l] : kWeights[l]) / c->d.h);
+    for (int d = 0; d < 3; ++d) {
+        a.lb[d] = c->cpml_local_set ? c->lcoef[d][0] : nullptr;
+        a.la[d] = c->cpml_local_set ? c->lcoef[d][1] : nullptr;
+    }
     a.dtr = (float)(c->d.dt * c->vscale);   // rho = 1
     a.nbr = c->var_rho ? c->nbr : nullptr;
     a.sscale = c->sscale;
@@ -750,6 +759,9 @@ int fdtd_create(const fdtd_desc *desc, void *workspace, size_t workspace_bytes, 
     c->kdt = (float *)(w + L.kdt);
     c->nbr = (float *)(w + L.nbr);
     c->coef = (float *)(w + L.coef);
+    for (int d = 0; d < 3; ++d)
+        for (int k = 0; k < 2; ++k)
+            c->lcoef[d][k] = desc->cpml_local ? (float *)(w + L.lcoef[d][k]) : nullptr;
     c->wavelet = (float *)(w + L.wav);
     c->src = (int *)(w + L.src);
     c->rec = (int4 *)(w + L.rec);
@@ -875,6 +887,7 @@ int fdtd_set_cpml(fdtd_ctx *c, double R, double kappa_max, double alpha_frac, in
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->cpml_set = true;
     c->cpml_ska = false;
+    c->cpml_local_set = false;
     return FDTD_OK;
 }
 
@@ -899,6 +912,32 @@ int fdtd_set_anisotropy(fdtd_ctx *c, const double kr[3])
     return FDTD_OK;
 }
 
+int fdtd_set_cpml_local(fdtd_ctx *c, const float *vel, double R, double kappa_max, double alpha_frac, int q)
+{
+    if (!c || !vel)
+        return fail(c, FDTD_EINVAL, "NULL argument");
+    if (!c->d.cpml_local)
+        return fail(c, FDTD_ESTATE, "the context was created without cpml_local");
+    if (c->d.storage != FDTD_F32)
+        return fail(c, FDTD_EUNSUPPORTED, "the local grading is provided for FP32 storage only");
+    if (c->staggered)
+        return fail(c, FDTD_EUNSUPPORTED, "the local grading is provided for the collocated form only");
+    if (!c->model_set)
+        return fail(c, FDTD_ESTATE, "fdtd_set_cpml_local needs fdtd_set_model first");
+    // the 1D tables keep 1/kappa (and b, a graded with c_max for reference)
+    int st = fdtd_set_cpml(c, R, kappa_max, alpha_frac, q, c->c_max);
+    if (st != FDTD_OK)
+        return st;
+    unsigned bad = 0;
+    CUDA_TRY(c, launch_local_coef(c, vel, R, kappa_max, alpha_frac, q));
+    CUDA_TRY(c, cudaMemcpyAsync(&bad, c->minmax + 2, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (bad)
+        return fail(c, FDTD_EINVAL, "%u slab nodes have a velocity that is not finite and positive", bad);
+    c->cpml_local_set = true;
+    return FDTD_OK;
+}
+
 int fdtd_set_staggered(fdtd_ctx *c, int on)
 {
     if (!c)
@@ -913,6 +952,8 @@ int fdtd_set_staggered(fdtd_ctx *c, int on)
         return fail(c, FDTD_EUNSUPPORTED, "the staggered form is provided for constant density only");
     if (on && c->cpml_ska)
         return fail(c, FDTD_EUNSUPPORTED, "learned profiles are provided for the collocated form only");
+    if (on && c->cpml_local_set)
+        return fail(c, FDTD_EUNSUPPORTED, "the local grading is provided for the collocated form only");
     const bool old = c->staggered;
     c->staggered = on != 0;
     if (c->model_set) {
@@ -940,6 +981,7 @@ int fdtd_set_cpml_ska(fdtd_ctx *c, const float *ska)
     CUDA_TRY(c, launch_ska_to_coef(c, ska, L));
     c->cpml_set = true;
     c->cpml_ska = true;
+    c->cpml_local_set = false;
     return FDTD_OK;
 }
 
@@ -1097,6 +1139,8 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
         return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the isotropic system only");
     if (c->staggered)
         return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the collocated form only");
+    if (c->cpml_local_set)
+        return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the 1D CPML grading only");
     const bool want_prof = grad_cpml != nullptr;
     const int nmax = nmax_of(c->g);
     CUDA_TRY(c, cudaMemsetAsync(c->gradK, 0, (size_t)c->d.nshots * c->g.vol * 4, c->stream));

@@ -2,6 +2,8 @@
 // caller's dense arrays and the internal (pitched / slab-compact, possibly
 // 16-bit) layout, FP64 reductions, the learned-CPML coefficient map and its
 // network (forward, backward, Adam).
+#include <cmath>
+
 #include "fdtd_internal.cuh"
 
 namespace fdtd {
@@ -46,6 +48,71 @@ __global__ void model_kernel(const float *__restrict__ vel, const float *__restr
     atomicMax(&minmax[1], vmax);
     if (bad)
         atomicAdd(&minmax[2], bad);
+}
+
+// ---------------------------------------------------------------------------
+// local-velocity CPML grading: b, a of every node of the d-slab from the
+// velocity c at that node, sigma_max(c) = -(q+1) c ln R / (2 L h) with the
+// face's own L, sigma = sigma_max rho^q, kappa = 1 + (kmax - 1) rho^q,
+// alpha = afrac sigma_max (1 - rho) at the node's normalised depth rho along
+// d; written in the slab layout (the caller zeroes the padding first).
+// ---------------------------------------------------------------------------
+__global__ void local_coef_kernel(const float *__restrict__ vel, Geom g, int d, double h, double dt, double lnR,
+                                  double kmax, double afrac, int q, float *__restrict__ lb, float *__restrict__ la,
+                                  unsigned *bad)
+{
+    const long long n = (long long)g.nz * g.ny * g.nx;
+    const int na = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+    const int lo = g.lo[d], hi = g.hi[d];
+    unsigned nbad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx);
+        const long long zy = i / g.nx;
+        const int y = (int)(zy % g.ny), z = (int)(zy / g.ny);
+        const int j = d == 0 ? x : (d == 1 ? y : z);
+        if (!in_slab(j, na, lo, hi))
+            continue;
+        const int L = j < lo ? lo : hi;
+        const double rho = j < lo ? double(lo - j) / L : double(j - (na - 1 - hi)) / L;
+        const double c = vel[i];
+        double b = 0.0, a = 0.0;
+        if (c > 0.0 && isfinite(c)) {
+            const double smax = -(q + 1) * c * lnR / (2.0 * L * h);
+            double rq = 1.0;
+            for (int k = 0; k < q; ++k)
+                rq *= rho;
+            const double sigma = smax * rq, kappa = 1.0 + (kmax - 1.0) * rq, alpha = afrac * smax * (1.0 - rho);
+            b = exp(-(sigma / kappa + alpha) * dt);
+            const double den = kappa * (sigma + kappa * alpha);
+            a = (sigma > 0.0 && den != 0.0) ? sigma * (b - 1.0) / den : 0.0;
+        } else {
+            nbad++;
+        }
+        const long long k = slab_index(g, d, z, y, x);
+        lb[k] = (float)b;
+        la[k] = (float)a;
+    }
+    if (nbad)
+        atomicAdd(bad, nbad);
+}
+
+cudaError_t launch_local_coef(const fdtd_ctx *c, const float *vel, double R, double kmax, double afrac, int q)
+{
+    cudaError_t e = cudaMemsetAsync(c->minmax + 2, 0, 4, c->stream);
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+        if (c->g.slab[d] == 0)
+            continue;
+        e = cudaMemsetAsync(c->lcoef[d][0], 0, (size_t)c->g.slab[d] * 4, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c->lcoef[d][1], 0, (size_t)c->g.slab[d] * 4, c->stream);
+        if (e == cudaSuccess) {
+            local_coef_kernel<<<1216, 256, 0, c->stream>>>(vel, c->g, d, c->d.h, c->d.dt, std::log(R), kmax, afrac, q,
+                                                           c->lcoef[d][0], c->lcoef[d][1], c->minmax + 2);
+            e = cudaGetLastError();
+        }
+    }
+    return e;
 }
 
 cudaError_t launch_model(fdtd_ctx *c, const float *vel, const float *rho)

@@ -312,6 +312,7 @@ struct StepArgs {
     void *psip[3];                  // updated in place
     const float *cb[3], *ca[3], *ck[3];   // b, a, 1/kappa per node of each axis
     const float *cbv[3], *cav[3], *ckv[3];   // the same for the velocity update (half nodes when staggered)
+    const float *lb[3], *la[3];     // local grading: b, a per slab node (slab layout, shared by shots), or null
     float c[4];                     // a_l / h
     float dtr;                      // dt * vscale / rho (velocity update, constant density)
     const float *nbr;               // [vol] -dt * vscale / rho per node (variable density), or null
@@ -356,6 +357,8 @@ struct fdtd_ctx {
     bool var_rho;           // fdtd_set_model was given a density
     double kr[3];           // elliptic anisotropy factors (1, 1, 1: isotropic)
     bool staggered;         // the staggered (Yee) form: v_d at half nodes
+    float *lcoef[3][2];     // local grading: b, a per slab node of axis d (slab layout), if reserved
+    bool cpml_local_set;    // fdtd_set_cpml_local is in force
     float *coef;            // [2][3][3][nmax]: b, a, 1/kappa per axis and node, then at the half nodes
     float *wavelet;         // [nshots][nt_max]
     int nt_w;

@@ -265,6 +265,10 @@ __device__ __forceinline__ V4 ld_nbr(const float *nbr, long long o, bool ok)
 template <typename T>
 __device__ __forceinline__ V4 ldg_v4(const T *p) { return to_v4(Io<T>::ld4(p)); }
 
+// per-node CPML coefficients of 4 nodes (local grading tables, read-only)
+__device__ __forceinline__ V4 ldc4(const float *p) { return to_v4(Io<float>::ldg4(p)); }
+__device__ __forceinline__ float2 ldc2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+
 // store of a step output, not read again within this step: L2 evict-first
 template <typename T>
 __device__ __forceinline__ void st_out(T *p, const F4 &v)
@@ -339,8 +343,10 @@ __host__ __device__ __forceinline__ int chunk_count(const StepArgs &A)
 // variables, no coefficient tables and no masks at the grid edge.  The same
 // arithmetic in the same order runs in both forms.  kStag selects the
 // staggered (Yee) neighbour sets; the velocity CPML then reads the half-node
-// coefficients sCxv, sCyv, A.cbv.. (the node tables otherwise).
-template <typename T, bool kEdge, bool kRho, bool kStag>
+// coefficients sCxv, sCyv, A.cbv.. (the node tables otherwise).  kLocal
+// takes b and a of every slab node from the per-node tables A.lb, A.la
+// (local-velocity grading; 1/kappa stays the 1D table).
+template <typename T, bool kEdge, bool kRho, bool kStag, bool kLocal>
 __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorMap &mPq, const CUtensorMap &mVX,
                                           const CUtensorMap &mVY, const CUtensorMap &mVZ, const CUtensorMap &mK,
                                           const StepArgs &A, int z0, int z1, unsigned char *smem,
@@ -516,8 +522,14 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
         // slab loads of the next iteration do not wait on HBM
         if (kEdge) {
             const int tn = t + 1, zn = zv + 1;
-            if (row_ok && zn < G.nz && zn >= 0 && in_slab(zn, G.nz, G.lo[2], G.hi[2]))
-                prefetch_l2(psiv_in[2] + slab_index(G, 2, zn, gy, gx));
+            if (row_ok && zn < G.nz && zn >= 0 && in_slab(zn, G.nz, G.lo[2], G.hi[2])) {
+                const long long i = slab_index(G, 2, zn, gy, gx);
+                prefetch_l2(psiv_in[2] + i);
+                if (kLocal) {
+                    prefetch_l2(A.lb[2] + i);
+                    prefetch_l2(A.la[2] + i);
+                }
+            }
             if (tn >= z0 && tn < z1) {
                 if (row_ok && in_slab(tn, G.nz, G.lo[2], G.hi[2]))
                     prefetch_l2(psip[2] + slab_index(G, 2, tn, gy, gx));
@@ -526,11 +538,19 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                         const long long i = slab_index(G, 0, tn, gy, gx);
                         prefetch_l2(psiv_in[0] + i);
                         prefetch_l2(psip[0] + i);
+                        if (kLocal) {
+                            prefetch_l2(A.lb[0] + i);
+                            prefetch_l2(A.la[0] + i);
+                        }
                     }
                     if (own_y) {
                         const long long i = slab_index(G, 1, tn, gy, gx);
                         prefetch_l2(psiv_in[1] + i);
                         prefetch_l2(psip[1] + i);
+                        if (kLocal) {
+                            prefetch_l2(A.lb[1] + i);
+                            prefetch_l2(A.la[1] + i);
+                        }
                     }
                     if (halo_psi_y)
                         prefetch_l2(psiv_in[1] + slab_index(G, 1, tn, yh_y, yh_x));
@@ -579,7 +599,8 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                 if (zs_v) {
                     const long long izv = slab_index(G, 2, zv, gy, gx);
                     const V4 psvz = ldg_v4(psiv_in[2] + izv);
-                    const V4 b = splat4(__ldg(A.cbv[2] + zv)), a = splat4(__ldg(A.cav[2] + zv)),
+                    const V4 b = kLocal ? ldc4(A.lb[2] + izv) : splat4(__ldg(A.cbv[2] + zv)),
+                             a = kLocal ? ldc4(A.la[2] + izv) : splat4(__ldg(A.cav[2] + zv)),
                              k = splat4(__ldg(A.ckv[2] + zv));
                     if (owned && stape[2])
                         tape4(stape[2], izv, 0, gz, psvz);
@@ -613,7 +634,8 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     const V4 psvx = ldg_v4(psiv_in[0] + ix);
                     if (stape[0])
                         tape4(stape[0], ix, 0, g, psvx);
-                    const V4 pn = cpml4(g, psvx, ldsf(&sCxv[0][cx]), ldsf(&sCxv[1][cx]), ldsf(&sCxv[2][cx]));
+                    const V4 pn = cpml4(g, psvx, kLocal ? ldc4(A.lb[0] + ix) : ldsf(&sCxv[0][cx]),
+                                        kLocal ? ldc4(A.la[0] + ix) : ldsf(&sCxv[1][cx]), ldsf(&sCxv[2][cx]));
                     st_out(psiv_out[0] + ix, to_f4(pn));
                 }
                 V4 vn = kRho ? fmav(nbo, g, lds<T>(S + L::OFF_VX, ty * L::VXW + 4 * tx + 8))
@@ -639,7 +661,8 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     const V4 psvy = ldg_v4(psiv_in[1] + iy);
                     if (stape[1])
                         tape4(stape[1], iy, 0, g, psvy);
-                    const V4 pn = cpml4(g, psvy, splat4(sCyv[0][ty + 4]), splat4(sCyv[1][ty + 4]), splat4(sCyv[2][ty + 4]));
+                    const V4 pn = cpml4(g, psvy, kLocal ? ldc4(A.lb[1] + iy) : splat4(sCyv[0][ty + 4]),
+                                        kLocal ? ldc4(A.la[1] + iy) : splat4(sCyv[1][ty + 4]), splat4(sCyv[2][ty + 4]));
                     st_out(psiv_out[1] + iy, to_f4(pn));
                 }
                 V4 vn = kRho ? fmav(nbo, g, lds<T>(S + L::OFF_VY, (ty + 4) * TX + 4 * tx))
@@ -662,8 +685,10 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                 float2 g = dnb2(m, p, C);
                 const int r = yh_y - y0 + 4;
                 if (halo_psi_y) {
-                    const float2 psh = Io<T>::ld2(psiv_in[1] + slab_index(G, 1, t, yh_y, yh_x));
-                    cpml2(g, psh, make_float2(sCyv[0][r], sCyv[0][r]), make_float2(sCyv[1][r], sCyv[1][r]),
+                    const long long ih = slab_index(G, 1, t, yh_y, yh_x);
+                    const float2 psh = Io<T>::ld2(psiv_in[1] + ih);
+                    cpml2(g, psh, kLocal ? ldc2(A.lb[1] + ih) : make_float2(sCyv[0][r], sCyv[0][r]),
+                          kLocal ? ldc2(A.la[1] + ih) : make_float2(sCyv[1][r], sCyv[1][r]),
                           make_float2(sCyv[2][r], sCyv[2][r]));
                 }
                 float2 vn = fma2(kRho ? nbh : ndtr, g, lds2<T>(S + L::OFF_VY, r * TX + (yh_x - x0)));
@@ -679,9 +704,11 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                 float2 g = kStag ? sdf2(P0, P1, P2, P3, P4, C) : dx2(P0, P1, P2, P3, P4, C);
                 const int cx = xh_x - x0 + 4;
                 if (halo_psi_x) {
-                    const float2 psh = Io<T>::ld2(psiv_in[0] + slab_index(G, 0, t, xh_y, xh_x));
-                    cpml2(g, psh, *reinterpret_cast<const float2 *>(&sCxv[0][cx]),
-                          *reinterpret_cast<const float2 *>(&sCxv[1][cx]), *reinterpret_cast<const float2 *>(&sCxv[2][cx]));
+                    const long long ih = slab_index(G, 0, t, xh_y, xh_x);
+                    const float2 psh = Io<T>::ld2(psiv_in[0] + ih);
+                    cpml2(g, psh, kLocal ? ldc2(A.lb[0] + ih) : *reinterpret_cast<const float2 *>(&sCxv[0][cx]),
+                          kLocal ? ldc2(A.la[0] + ih) : *reinterpret_cast<const float2 *>(&sCxv[1][cx]),
+                          *reinterpret_cast<const float2 *>(&sCxv[2][cx]));
                 }
                 float2 vn = fma2(kRho ? nbh : ndtr, g, lds2<T>(S + L::OFF_VX, (xh_y - y0) * L::VXW + lx));
                 if (kEdge) {
@@ -723,7 +750,8 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                 const V4 pspx = ldg_v4(psip[0] + ix);
                 if (stape[0])
                     tape4(stape[0], ix, 2, hx4, pspx);
-                const V4 pn = cpml4(hx4, pspx, ldsf(&sCx[0][cx]), ldsf(&sCx[1][cx]), ldsf(&sCx[2][cx]));
+                const V4 pn = cpml4(hx4, pspx, kLocal ? ldc4(A.lb[0] + ix) : ldsf(&sCx[0][cx]),
+                                    kLocal ? ldc4(A.la[0] + ix) : ldsf(&sCx[1][cx]), ldsf(&sCx[2][cx]));
                 st_out(psip[0] + ix, to_f4(pn));
             }
             if (own_y) {
@@ -731,7 +759,8 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                 const V4 pspy = ldg_v4(psip[1] + iy);
                 if (stape[1])
                     tape4(stape[1], iy, 2, hy4, pspy);
-                const V4 pn = cpml4(hy4, pspy, splat4(sCy[0][ty + 4]), splat4(sCy[1][ty + 4]), splat4(sCy[2][ty + 4]));
+                const V4 pn = cpml4(hy4, pspy, kLocal ? ldc4(A.lb[1] + iy) : splat4(sCy[0][ty + 4]),
+                                    kLocal ? ldc4(A.la[1] + iy) : splat4(sCy[1][ty + 4]), splat4(sCy[2][ty + 4]));
                 st_out(psip[1] + iy, to_f4(pn));
             }
             if (zs_p) {
@@ -739,8 +768,8 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                 const V4 pspz = ldg_v4(psip[2] + izp);
                 if (stape[2])
                     tape4(stape[2], izp, 2, hz4, pspz);
-                const V4 pn = cpml4(hz4, pspz, splat4(__ldg(A.cb[2] + t)), splat4(__ldg(A.ca[2] + t)),
-                                    splat4(__ldg(A.ck[2] + t)));
+                const V4 pn = cpml4(hz4, pspz, kLocal ? ldc4(A.lb[2] + izp) : splat4(__ldg(A.cb[2] + t)),
+                                    kLocal ? ldc4(A.la[2] + izp) : splat4(__ldg(A.ca[2] + t)), splat4(__ldg(A.ck[2] + t)));
                 st_out(psip[2] + izp, to_f4(pn));
             }
             // nkdt holds -dt K / vscale (zero beyond the grid)
@@ -789,7 +818,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
     }
 }
 
-template <typename T, bool kRho, bool kStag>
+template <typename T, bool kRho, bool kStag, bool kLocal>
 __global__ void __launch_bounds__(NTHREADS, kMinBlocks)
     fdtd_step_kernel(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mPq,
                      const __grid_constant__ CUtensorMap mVX, const __grid_constant__ CUtensorMap mVY,
@@ -813,38 +842,44 @@ __global__ void __launch_bounds__(NTHREADS, kMinBlocks)
     const bool interior = x0 - 4 >= G.lo[0] && x0 + TX + 4 <= G.nx - G.hi[0] && y0 - 4 >= G.lo[1] &&
                           y0 + TY + 4 <= G.ny - G.hi[1] && z0 - 4 >= G.lo[2] && z1 + 4 <= G.nz - G.hi[2];
     if (interior)
-        step_body<T, false, kRho, kStag>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy, vx, vy);
+        step_body<T, false, kRho, kStag, false>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy, vx, vy);
     else
-        step_body<T, true, kRho, kStag>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy, vx, vy);
+        step_body<T, true, kRho, kStag, kLocal>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, smem, sCx, sCy, vx, vy);
 }
 
-template <typename T, bool kRho, bool kStag>
+template <typename T, bool kRho, bool kStag, bool kLocal>
 static cudaError_t launch_step_tr(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream)
 {
     using L = StageLayout<T>;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(fdtd_step_kernel<T, kRho, kStag>,
+        cudaError_t e = cudaFuncSetAttribute(fdtd_step_kernel<T, kRho, kStag, kLocal>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
         if (e != cudaSuccess)
             return e;
         attr_done = true;
     }
     dim3 grid(c->tiles_x * c->tiles_y, chunk_count(a), c->d.nshots);
-    fdtd_step_kernel<T, kRho, kStag><<<grid, NTHREADS, L::SMEM, stream>>>(
+    fdtd_step_kernel<T, kRho, kStag, kLocal><<<grid, NTHREADS, L::SMEM, stream>>>(
         c->maps[set][0], c->maps[set][1], c->maps[set][2], c->maps[set][3], c->maps[set][4], c->mapK, a);
     return cudaGetLastError();
 }
 
 // a.nbr selects the variable-density form, c->staggered the staggered one
-// (FP32 storage and constant density only; the API enforces both)
+// (FP32 storage and constant density only), a.lb[0] the local grading (FP32
+// storage, collocated); the API enforces these combinations
 template <typename T>
 static cudaError_t launch_step_t(const fdtd_ctx *c, const StepArgs &a, int set, cudaStream_t stream)
 {
-    if constexpr (std::is_same<T, float>::value)
+    if constexpr (std::is_same<T, float>::value) {
         if (c->staggered)
-            return a.nbr ? cudaErrorInvalidValue : launch_step_tr<T, false, true>(c, a, set, stream);
-    return a.nbr ? launch_step_tr<T, true, false>(c, a, set, stream) : launch_step_tr<T, false, false>(c, a, set, stream);
+            return (a.nbr || a.lb[0]) ? cudaErrorInvalidValue : launch_step_tr<T, false, true, false>(c, a, set, stream);
+        if (a.lb[0])
+            return a.nbr ? launch_step_tr<T, true, false, true>(c, a, set, stream)
+                         : launch_step_tr<T, false, false, true>(c, a, set, stream);
+    }
+    return a.nbr ? launch_step_tr<T, true, false, false>(c, a, set, stream)
+                 : launch_step_tr<T, false, false, false>(c, a, set, stream);
 }
 
 // One step over z in [a.zbase, a.zend) on `stream`; `set` is the ping-pong
@@ -865,8 +900,8 @@ template <typename T>
 static int occupancy_t(int *blocks)
 {
     using L = StageLayout<T>;
-    cudaFuncSetAttribute(fdtd_step_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fdtd_step_kernel<T, false, false>, NTHREADS, L::SMEM) ==
+    cudaFuncSetAttribute(fdtd_step_kernel<T, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fdtd_step_kernel<T, false, false, false>, NTHREADS, L::SMEM) ==
                    cudaSuccess
                ? 0
                : -1;

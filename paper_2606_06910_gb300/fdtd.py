@@ -47,7 +47,8 @@ class Fdtd:
     """
 
     def __init__(self, shape, h, dt, *, nshots=1, cpml_cells=0, storage="f32", nt_max=1,
-                 nrec_max=0, checkpoint_every=0, cpml_grad=False, tblock_k=1, device=None, stream=None):
+                 nrec_max=0, checkpoint_every=0, cpml_grad=False, tblock_k=1, cpml_local=False, device=None,
+                 stream=None):
         self.lib = _lib.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda")
         if self.device.type != "cuda":
@@ -76,6 +77,7 @@ class Fdtd:
         d.nrec_max = int(nrec_max)
         d.checkpoint_every = int(checkpoint_every)
         d.cpml_grad = 1 if cpml_grad else 0
+        d.cpml_local = 1 if cpml_local else 0
         d.stream = ctypes.c_void_p(stream.cuda_stream)
         self._desc = d
         nbytes = ctypes.c_size_t(0)
@@ -130,6 +132,13 @@ class Fdtd:
         speed along axis d is c sqrt(kr_d)."""
         arr = (ctypes.c_double * 3)(*[float(v) for v in kr])
         self._check(self.lib.fdtd_set_anisotropy(self.ctx, ctypes.cast(arr, ctypes.c_void_p)))
+
+    def set_cpml_local(self, vel: torch.Tensor, R=1e-8, kappa_max=5.0, alpha_frac=0.05, q=3):
+        """Local-velocity grading: sigma_max from the velocity at each slab
+        node (needs cpml_local=True at construction and set_model first)."""
+        _need(vel, self.shape, self.device, "vel")
+        self._check(self.lib.fdtd_set_cpml_local(self.ctx, _ptr(vel), float(R), float(kappa_max),
+                                                 float(alpha_frac), int(q)))
 
     def set_staggered(self, on: bool = True):
         """Staggered (Yee) form: v_d at the half nodes i + 1/2, staggered

@@ -50,7 +50,7 @@ def oracle_state(shape, state):
     return st
 
 
-def subbox_point(full_state, vel, h, dt, cells, c_ref, point, radius, nsteps, R=1e-8, staggered=False):
+def subbox_point(full_state, vel, h, dt, cells, c_ref, point, radius, nsteps, R=1e-8, staggered=False, local=False):
     """Oracle values of every field at `point` after nsteps, computed on the
     sub-box of the given radius around it (exact when radius >= 8 nsteps: the
     step's dependence radius is 2r = 8 nodes per axis)."""
@@ -67,7 +67,8 @@ def subbox_point(full_state, vel, h, dt, cells, c_ref, point, radius, nsteps, R=
         prof.append({k: np.ascontiguousarray(prof_full[d][k][a:b])
                      for k in ("slab", "b", "a", "kinv", "bv", "av", "kinvv")})
     v = np.asarray(vel[z0:z1, y0:y1, x0:x1], dtype=np.float64)
-    g = O.Grid(v * v, h, dt, prof, staggered=staggered)
+    lp = O.local_profiles(v, cells, h, dt, R=R, full_shape=vel.shape, origin=(z0, y0, x0)) if local else None
+    g = O.Grid(v * v, h, dt, prof, staggered=staggered, local=lp)
     st = O.State(v.shape)
     for k in FIELDS:
         st[k] = np.asarray(full_state[k][z0:z1, y0:y1, x0:x1], dtype=np.float64)

@@ -42,7 +42,7 @@ def test_exports_every_declared_function(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.fdtd_abi_version() == 1
+    assert lib.fdtd_abi_version() == 2
     for s in range(9):
         assert lib.fdtd_status_string(s)
     assert lib.fdtd_status_string(99) == b"unknown status"

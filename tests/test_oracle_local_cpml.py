@@ -158,3 +158,18 @@ def test_pressure_stage_uses_each_nodes_coefficients():
         slab = np.broadcast_to(prof[d]["slab"].reshape(shp).astype(bool), shape)
         expect = np.where(slab, lp[d]["a"] * delta, 0.0)
         assert np.max(np.abs(st["psip_" + ax] - expect)) <= 1e-12 * np.max(np.abs(expect)), ax
+
+
+def test_sub_box_profiles_equal_the_full_grids():
+    """local_profiles on a box of a larger grid (its origin given) equals the
+    box cut out of the full grid's profiles."""
+    rng = np.random.default_rng(3)
+    shape, cells, h = (20, 22, 24), (4, 5, 3, 6, 5, 4), 10.0
+    vel = rng.uniform(1500.0, 4000.0, size=shape)
+    full = O.local_profiles(vel, cells, h, 1e-3, R=1e-6)
+    for o, e in (((0, 0, 0), (9, 10, 11)), ((11, 7, 13), (20, 22, 24)), ((3, 4, 5), (17, 18, 19))):
+        box = tuple(slice(a, b) for a, b in zip(o, e))
+        part = O.local_profiles(vel[box], cells, h, 1e-3, R=1e-6, full_shape=shape, origin=o)
+        for d in range(3):
+            for k in ("b", "a", "sigma"):
+                assert np.array_equal(part[d][k], full[d][k][box]), (o, d, k)
