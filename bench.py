@@ -347,7 +347,8 @@ def form_tblock(dev, nsteps=96, warm=8):
         out[f"k{k}"] = entry
         del sim, p
         torch.cuda.empty_cache()
-    return {"workload": f"layered512, {warm} + {nsteps} timed steps, z bands of 48 planes", "unit": UNIT, **out}
+    return {"workload": f"layered512, {warm} + {nsteps} timed steps, z bands of 96 planes in 32-plane chunks",
+            "unit": UNIT, **out}
 
 
 def form_density(dev, nsteps=96, warm=8):

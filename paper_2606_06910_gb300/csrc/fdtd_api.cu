@@ -418,14 +418,14 @@ bool fault_is(const char *what)
 }
 
 // Streams and events of temporal blocking (tblock_k > 1).  The band height
-// is 48 planes unless FDTD_TBAND says otherwise; it is never below 8, the
+// is 96 planes unless FDTD_TBAND says otherwise; it is never below 8, the
 // dependence radius of one step along z.
 int make_tblock(fdtd_ctx *c)
 {
     const int k = c->d.tblock_k;
     if (k <= 1)
         return FDTD_OK;
-    int band = 48;
+    int band = 96;
     if (const char *e = getenv("FDTD_TBAND")) {
         const int v = atoi(e);
         if (v > 0)
@@ -528,6 +528,14 @@ bool needs_ckpt(const fdtd_ctx *c, int t)
 int launch_blocks(fdtd_ctx *c, int m)
 {
     const int k = c->d.tblock_k, nb = c->tb_nb;
+    // planes per CTA within a band launch: the single-step chunk target (32
+    // planes FP32, 96 16-bit), or FDTD_TBCHUNK.  Several chunks per band give
+    // each launch more CTAs than one wave, so that the k streams' launches
+    // backfill each other instead of starting together with a ragged tail.
+    int tb_chunk = c->d.storage == FDTD_F32 ? 32 : 96;
+    if (const char *e = getenv("FDTD_TBCHUNK"))
+        if (atoi(e) > 0)
+            tb_chunk = std::max(8, atoi(e));
     auto ev = [&](int s, int b) { return c->tb_ev[(size_t)s * nb + b]; };
     CUDA_TRY(c, cudaEventRecord(c->tb_entry, c->stream));
     for (int s = 0; s < k; ++s)
@@ -549,7 +557,9 @@ int launch_blocks(fdtd_ctx *c, int m)
                 a.t = c->t + s;
                 a.zbase = b * c->tb_band;
                 a.zend = b == nb - 1 ? c->g.nz : (b + 1) * c->tb_band;
-                a.zchunk = a.zend - a.zbase;
+                // chunks of at most tb_chunk planes, equal within the band
+                const int hb = a.zend - a.zbase, nch = (hb + tb_chunk - 1) / tb_chunk;
+                a.zchunk = (hb + nch - 1) / nch;
                 a.zmid0 = a.zbase;
                 a.zmid1 = a.zend;
                 a.p_in = c->p[set];
