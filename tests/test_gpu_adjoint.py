@@ -245,3 +245,34 @@ def test_adjoint_state_matches_oracle_multi_tile(monkeypatch, shape, cells, zchu
     gref = (refs[0][1] + refs[1][1]) * 2.0 * vel.astype(np.float64)
     e2, em = rel_errors(grad.cpu().numpy(), gref)
     assert e2 <= 1e-4 and em <= 1e-3, (e2, em)
+
+
+def test_dot_product_identity_full_size_256x16():
+    """The adjoint workload's grid and launch configuration (256^3, 20-cell
+    layers, 16 shots): <F x, y> = <x, F^T y> over 6 steps with checkpoints
+    every 3, for random x and y of every shot, generated on the device from a
+    seeded generator; the sums are taken in FP64."""
+    Fdtd = _Fdtd()
+    w = synth.preset("adjoint256")
+    shape, cells, nshots, n = w.shape, w.cpml_cells, w.nshots, 6
+    sim = Fdtd(shape, w.h, w.dt, nshots=nshots, cpml_cells=cells, nt_max=8, checkpoint_every=3)
+    sim.set_model(torch.from_numpy(w.velocity()).cuda())
+    sim.set_cpml(R=w.R, c_ref=w.vmax)
+    sc = state_scales(w.h, w.dt)
+    scale = {"p": sc["p_scale"], "vx": sc["v_scale"], "vy": sc["v_scale"], "vz": sc["v_scale"]}
+    gen = torch.Generator(device="cuda").manual_seed(2024)
+    x, y = {}, {}
+    for s in range(nshots):
+        for k in FIELDS:
+            f = scale.get(k, sc["psiv_scale"] if k.startswith("psiv") else sc["psip_scale"])
+            sim.set(k, f * torch.randn(shape, device="cuda", generator=gen), s)
+            sim.set("adj_" + k, torch.randn(shape, device="cuda", generator=gen), s)
+            x[s, k] = sim.get(k, s).double()      # as stored (memory variables only in their slabs)
+            y[s, k] = sim.get("adj_" + k, s).double()
+    sim.step(n)
+    lhs = sum(float(torch.sum(sim.get(k, s).double() * y[s, k])) for s in range(nshots) for k in FIELDS)
+    del y
+    sim.adjoint(n)
+    rhs = sum(float(torch.sum(x[s, k] * sim.get("adj_" + k, s).double())) for s in range(nshots) for k in FIELDS)
+    print(f"\n[adjoint 256^3 x 16] <Fx, y> = {lhs:.10e}, <x, F^T y> = {rhs:.10e}")
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs)), (lhs, rhs)

@@ -157,3 +157,61 @@ def test_learned_layer_beats_polynomial_layer_of_same_thickness():
           f"training J {res['J_first']:.3e} -> {res['J_last']:.3e}")
     assert res["J_last"] < res["J_first"]
     assert res["learned_eval"] < 0.9 * res["poly_eval"]
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 4e-3), ("bf16", 3e-2)])
+def test_16bit_full_size_1024_sampled_parity(storage, tol):
+    """The 16-bit forms' workload (1024^3 layered, 20-cell layers) in the
+    benchmark's launch configuration: a random state generated on the device
+    and stored in 16 bits, 2 steps, every field at sampled nodes (faces,
+    edges, corners, interior) against the oracle run on a sub-box of the
+    stored initial state.  Bound: tol x the field's scale (FP16 keeps 11
+    significant bits, BF16 8)."""
+    Fdtd = _Fdtd()
+    from tests.parity_util import FIELDS, state_scales
+    w = synth.preset("layered1024")
+    shape, cells, nsteps = w.shape, w.cpml_cells, 2
+    vel = w.velocity()
+    sim = Fdtd(shape, w.h, w.dt, cpml_cells=cells, nt_max=4, storage=storage)
+    sim.set_model(torch.from_numpy(vel).cuda())
+    sim.set_cpml(R=w.R, c_ref=w.vmax)
+    sc = state_scales(w.h, w.dt)
+    scale = {"p": sc["p_scale"], "vx": sc["v_scale"], "vy": sc["v_scale"], "vz": sc["v_scale"]}
+    gen = torch.Generator(device="cuda").manual_seed(77)
+    rng = np.random.default_rng(5)
+    pts = [(0, 0, 0), (1023, 1023, 1023), (0, 1023, 511), (19, 20, 21), (20, 19, 1004), (1003, 1004, 19),
+           (512, 512, 512), (511, 127, 128), (600, 31, 32), (200, 32, 1023), (33, 700, 127)]
+    pts += [tuple(int(v) for v in rng.integers(0, 1024, 3)) for _ in range(12)]
+    pts += [tuple(int(v) for v in rng.integers(1000, 1024, 3)) for _ in range(3)]
+    r = 8 * nsteps + 1
+    boxes = [tuple(slice(max(0, p[d] - r), min(shape[d], p[d] + r + 1)) for d in range(3)) for p in pts]
+    init = {i: {} for i in range(len(pts))}
+    fscale = {}
+    for k in FIELDS:
+        f = scale.get(k, sc["psiv_scale"] if k.startswith("psiv") else sc["psip_scale"])
+        sim.set(k, f * torch.randn(shape, device="cuda", generator=gen))
+        stored = sim.get(k)
+        fscale[k] = float(stored.abs().max())
+        for i, b in enumerate(boxes):
+            init[i][k] = stored[b].double().cpu().numpy()
+        del stored
+    sim.step(nsteps)
+    sim.sync()
+    prof_full = O.make_profiles(shape, cells, w.h, w.dt, w.vmax, R=w.R)
+    got = {k: sim.get(k) for k in FIELDS}
+    for i, (p, b) in enumerate(zip(pts, boxes)):
+        prof = []
+        for d in range(3):
+            sl = b[2 - d]
+            prof.append({q: np.ascontiguousarray(prof_full[d][q][sl]) for q in ("slab", "b", "a", "kinv")})
+        v = vel[b].astype(np.float64)
+        g = O.Grid(v * v, w.h, w.dt, prof)
+        st = O.State(v.shape)
+        for k in FIELDS:
+            st[k] = init[i][k]
+        O.run(g, st, nsteps)
+        loc = tuple(p[d] - b[d].start for d in range(3))
+        for k in FIELDS:
+            gv = float(got[k][p])
+            ref = st[k][loc]
+            assert abs(gv - ref) <= tol * max(fscale[k], 1e-30), (storage, p, k, gv, ref)
