@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--forms-only", action="store_true", help="measure only the forms (profiling runs)")
+    ap.add_argument("--variant", default="plain", choices=["plain", "staggered", "local", "density"],
+                    help="form of the main line's step (profiling runs of the forms; FP32): the staggered grid "
+                         "at CFL 0.4, the local-velocity CPML grading, or the density (c/1500)^(1/4)")
     ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock,density,aniso2d,staggered,local_cpml",
                     help="comma list of forms measured after the main line ('' for none)")
     return ap.parse_args()
@@ -136,16 +139,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def step_kernel_traffic(storage: str, shape):
+def step_kernel_traffic(storage: str, shape, variant: str = "plain"):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    scaled to this grid, or None when the kernel source changed since."""
+    scaled to this grid, or None when the kernel source changed since (forms
+    other than the plain one are keyed "<storage>-<variant>")."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     srcs = [os.path.join(ROOT, "paper_2606_06910_gb300", "csrc", f) for f in ("fdtd_step.cu", "fdtd_internal.cuh")]
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
     h = hashlib.sha256(b"".join(open(s, "rb").read() for s in srcs)).hexdigest()[:16]
-    e = d.get(storage)
+    e = d.get(storage if variant == "plain" else f"{storage}-{variant}")
     if not e or e.get("kernel_sha") != h:
         return None
     n_prof = float(np.prod(e["shape"]))
@@ -155,14 +159,17 @@ def step_kernel_traffic(storage: str, shape):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-def algorithmic_bytes(shape, cells, es):
+def algorithmic_bytes(shape, cells, es, variant="plain"):
     """Per launch: read p, v (3), K and write p, v (3): 8 stored words + one
     FP32 word per node; plus 4 stored words (psi_v and psi_p read and write)
-    per slab node and axis."""
+    per slab node and axis.  The density form reads one more FP32 word per
+    node (dt / rho); the local grading reads b and a (8 B) per slab node and
+    axis; the staggered form moves the same bytes."""
     nz, ny, nx = shape
     n = nx * ny * nz
     slab = (cells[0] + cells[1]) * ny * nz + (cells[2] + cells[3]) * nx * nz + (cells[4] + cells[5]) * nx * ny
-    return (8 * es + 4) * n + 4 * es * slab
+    extra = 4 * n if variant == "density" else (8 * slab if variant == "local" else 0)
+    return (8 * es + 4) * n + 4 * es * slab + extra
 
 
 def run_ours(args, rank, world, local):
@@ -178,15 +185,25 @@ def run_ours(args, rank, world, local):
     shape = w.shape
     vel_h = w.velocity()
     src = w.sources()
-    wav_h = synth.ricker(nt, w.dt, w.f0).astype(np.float32)[None, :]
+    variant = args.variant
+    if variant != "plain" and args.storage != "f32":
+        raise SystemExit("--variant needs --storage f32")
+    dt = 0.4 * w.h / w.c_max if variant == "staggered" else w.dt     # the staggered limit is 0.4488
+    wav_h = synth.ricker(nt, dt, w.f0).astype(np.float32)[None, :]
     stream = torch.cuda.current_stream(dev)
 
-    sim = Fdtd(shape, w.h, w.dt, cpml_cells=cells, storage=args.storage, nt_max=nt, device=dev, stream=stream)
+    sim = Fdtd(shape, w.h, dt, cpml_cells=cells, storage=args.storage, nt_max=nt, device=dev, stream=stream,
+               cpml_local=variant == "local")
     vel = torch.from_numpy(vel_h).to(dev)
     wav = torch.from_numpy(wav_h).to(dev)
-    sim.set_model(vel)
+    if variant == "staggered":
+        sim.set_staggered(True)
+    sim.set_model(vel, (vel / 1500.0) ** 0.25 if variant == "density" else None)
     if any(cells):
-        sim.set_cpml(R=w.R, kappa_max=w.kappa_max, alpha_frac=w.alpha_frac, q=w.q, c_ref=w.c_max)
+        if variant == "local":
+            sim.set_cpml_local(vel, R=w.R, kappa_max=w.kappa_max, alpha_frac=w.alpha_frac, q=w.q)
+        else:
+            sim.set_cpml(R=w.R, kappa_max=w.kappa_max, alpha_frac=w.alpha_frac, q=w.q, c_ref=w.c_max)
     sim.inject(src, wav)
 
     def one_step(evs=None):
@@ -231,15 +248,15 @@ def run_ours(args, rank, world, local):
     es = 4 if args.storage == "f32" else 2
     launches = args.steps * nt
     avg_launch_s = kernel_ms * 1e-3 / launches
-    bytes_launch = algorithmic_bytes(shape, cells, es)
+    bytes_launch = algorithmic_bytes(shape, cells, es, variant)
     achieved = bytes_launch / avg_launch_s / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = step_kernel_traffic(args.storage, shape)
+    traffic = step_kernel_traffic(args.storage, shape, variant)
 
     # end to end through the public API: pinned host model + wavelet in,
     # final pressure snapshot out, every step
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and variant == "plain":
         vel_pin = torch.from_numpy(vel_h).pin_memory()
         wav_pin = torch.from_numpy(wav_h).pin_memory()
         snap_pin = torch.empty(shape, dtype=torch.float32).pin_memory()
@@ -363,6 +380,7 @@ def form_density(dev, nsteps=96, warm=8):
     rho = (vel / 1500.0) ** 0.25
     npts = float(np.prod(w.shape))
     out = {}
+    peak, _ = measured_peaks()
     for name, r in (("constant", None), ("variable", rho)):
         sim = Fdtd(w.shape, w.h, w.dt, cpml_cells=w.cpml_cells, nt_max=w.nt, device=dev)
         sim.set_model(vel, r)
@@ -371,7 +389,9 @@ def form_density(dev, nsteps=96, warm=8):
         sim.step(warm)
         sim.sync()
         secs = _timed(sim.stream, lambda: sim.step(nsteps))
-        out[name] = {"value": round(npts * nsteps / secs / 1e6, 1), "ms_per_step": round(secs / nsteps * 1e3, 4)}
+        b = algorithmic_bytes(w.shape, w.cpml_cells, 4, "density" if r is not None else "plain")
+        out[name] = {"value": round(npts * nsteps / secs / 1e6, 1), "ms_per_step": round(secs / nsteps * 1e3, 4),
+                     "roofline_frac": round(b * nsteps / secs / 1e9 / peak, 4)}
         del sim
         torch.cuda.empty_cache()
     return {"workload": f"layered512, density (c/1500)^0.25, {warm} + {nsteps} timed steps", "unit": UNIT, **out}
@@ -421,6 +441,7 @@ def form_local_cpml(dev, nsteps=96, warm=8):
     vel = torch.from_numpy(w.velocity()).to(dev)
     npts = float(np.prod(w.shape))
     out = {}
+    peak, _ = measured_peaks()
     for name in ("1d", "local"):
         sim = Fdtd(w.shape, w.h, w.dt, cpml_cells=w.cpml_cells, nt_max=w.nt, cpml_local=name == "local", device=dev)
         sim.set_model(vel)
@@ -432,7 +453,9 @@ def form_local_cpml(dev, nsteps=96, warm=8):
         sim.step(warm)
         sim.sync()
         secs = _timed(sim.stream, lambda: sim.step(nsteps))
-        out[name] = {"value": round(npts * nsteps / secs / 1e6, 1), "ms_per_step": round(secs / nsteps * 1e3, 4)}
+        b = algorithmic_bytes(w.shape, w.cpml_cells, 4, "local" if name == "local" else "plain")
+        out[name] = {"value": round(npts * nsteps / secs / 1e6, 1), "ms_per_step": round(secs / nsteps * 1e3, 4),
+                     "roofline_frac": round(b * nsteps / secs / 1e9 / peak, 4)}
         del sim
         torch.cuda.empty_cache()
     return {"workload": f"layered512, {warm} + {nsteps} timed steps", "unit": UNIT, **out}
@@ -582,11 +605,14 @@ def oracle_sample(preset: str, nsteps: int, warm: int = 0):
 
 
 def workload_config(args, shape, cells, nt, world):
-    return {"workload": f"{args.preset}: {shape[0]}^3 layered 1500-4500 m/s, CPML {cells[0]} cells, "
-                        f"R=1e-8, 10 Hz Ricker, {nt} time steps per bench step",
-            "grid": list(shape), "time_steps_per_step": nt, "cpml_cells": list(cells),
-            "storage": args.storage, "parallelism": f"replicas x{world}",
-            "l2": "inputs larger than L2 (state >= 4 GB per replica)"}
+    out = {"workload": f"{args.preset}: {shape[0]}^3 layered 1500-4500 m/s, CPML {cells[0]} cells, "
+                       f"R=1e-8, 10 Hz Ricker, {nt} time steps per bench step",
+           "grid": list(shape), "time_steps_per_step": nt, "cpml_cells": list(cells),
+           "storage": args.storage, "parallelism": f"replicas x{world}",
+           "l2": "inputs larger than L2 (state >= 4 GB per replica)"}
+    if getattr(args, "variant", "plain") != "plain":
+        out["variant"] = args.variant
+    return out
 
 
 def run_reference(args, rank, world):
