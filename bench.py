@@ -22,6 +22,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -90,7 +91,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples: a temporary folder unless FDTD_CLOCKS_DIR names one
+        out_dir = os.environ.get("FDTD_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"fdtd_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
