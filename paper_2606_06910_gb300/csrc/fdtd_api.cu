@@ -492,6 +492,8 @@ StepArgs base_args(const fdtd_ctx *c)
         a.lb[d] = c->cpml_local_set ? c->lcoef[d][0] : nullptr;
         a.la[d] = c->cpml_local_set ? c->lcoef[d][1] : nullptr;
     }
+    // failure test (FDTD_FAULT=wait): one CTA's third stage gets no copies
+    a.fault_it = fault_is("wait") ? 2 : -1;
     a.dtr = (float)(c->d.dt * c->vscale);   // rho = 1
     a.nbr = c->var_rho ? c->nbr : nullptr;
     a.sscale = c->sscale;

@@ -32,10 +32,11 @@ constexpr double kStagWeights[4] = {1225.0 / 1024.0, -245.0 / 3072.0, 49.0 / 512
 constexpr unsigned ERR_TIMEOUT = 1u;
 constexpr unsigned ERR_NONFINITE = 2u;
 
-// bounded spin on an mbarrier: 2^21 polls (on the order of a second) before
-// giving up; a plane's copies normally land within microseconds
-constexpr unsigned WAIT_LIMIT = 1u << 21;
-constexpr unsigned WAIT_LIMIT_DRAIN = 1u << 18;
+// bounded spin on an mbarrier: 2^18 polls (about a second on GB300, where a
+// poll that finds the phase incomplete takes about 4 us) before giving up; a
+// plane's copies normally land within microseconds
+constexpr unsigned WAIT_LIMIT = 1u << 18;
+constexpr unsigned WAIT_LIMIT_DRAIN = 1u << 15;
 
 struct F4 {
     float v[4];
@@ -313,6 +314,7 @@ struct StepArgs {
     const float *cb[3], *ca[3], *ck[3];   // b, a, 1/kappa per node of each axis
     const float *cbv[3], *cav[3], *ckv[3];   // the same for the velocity update (half nodes when staggered)
     const float *lb[3], *la[3];     // local grading: b, a per slab node (slab layout, shared by shots), or null
+    int fault_it;                   // failure test: CTA (0, 0, 0) issues no copies for this iteration (-1: none)
     float c[4];                     // a_l / h
     float dtr;                      // dt * vscale / rho (velocity update, constant density)
     const float *nbr;               // [vol] -dt * vscale / rho per node (variable density), or null

@@ -468,8 +468,13 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
     }
     __syncthreads();
 
-    // Issue the loads of iteration `it` into its stage (thread 0 only).
+    // Issue the loads of iteration `it` into its stage (thread 0 only).  The
+    // failure test leaves one stage of CTA (0, 0, 0) without its copies, so
+    // that the bounded wait on it gives up (the kernel then reports
+    // ERR_TIMEOUT, drains its copies in flight and returns).
     auto issue = [&](int it) {
+        if (it == A.fault_it && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+            return;
         const int t = z0 - 8 + it;
         unsigned char *S = smem + (it % NSTAGE) * L::BYTES;
         uint64_t *b = &bar[it % NSTAGE];
