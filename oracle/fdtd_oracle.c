@@ -272,9 +272,11 @@ static void og_deriv_transpose_acc(const og_grid *g, const double *y, int axis, 
  *
  * The forward step, written as a sequence of assignments
  *   g_d  = D_d p ;  psiv_d' = b psiv_d + a g_d ;  v_d' = v_d - dt/rho (kinv g_d + psiv_d')
- *   h_d  = D_d v_d' ; psip_d' = b psip_d + a h_d ; p' = p - dt K sum_d (kinv h_d + psip_d')
- * (CPML terms only inside the d-slab), is transposed assignment by assignment
- * in reverse order.  The source term is a constant and has no adjoint.
+ *   h_d  = D_d v_d' ; psip_d' = b psip_d + a h_d ;
+ *   p' = p - dt K sum_d kr_d (kinv h_d + psip_d')
+ * (CPML terms only inside the d-slab; kr_d = 1 unless anisotropic), is
+ * transposed assignment by assignment in reverse order.  The source term is a
+ * constant and has no adjoint.
  * Collocated form with 1D profiles only (g->staggered = 0, bn = an = NULL).
  */
 void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
@@ -330,9 +332,10 @@ void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
                 double lp = adj->p[i];
                 if (gradK)
                     gradK[i] += -g->dt * s_all[i] * lp;
-                double q = -g->dt * g->K[i] * lp;   /* adjoint of the bracket */
+                double q0 = -g->dt * g->K[i] * lp;   /* adjoint of the bracket sum */
                 for (int d = 0; d < 3; d++) {
                     long k = og_axis_index(d, z, y, x);
+                    double q = g->kr[d] * q0;         /* adjoint of axis d's bracket */
                     if (g->slab[d][k]) {
                         double lpsi = adj->psip[d][i] + q;   /* total adjoint of psip_d' */
                         lam_h[d][i] = g->kinv[d][k] * q + g->a[d][k] * lpsi;

@@ -301,8 +301,7 @@ class Grid:
 
     kr: elliptic anisotropy, (x, y, z) factors of the modulus in the
     pressure update, p' = p - dt K sum_d kr_d [...]_d; the axis velocities are
-    c sqrt(kr_d) (the 2D demo of Sec. 5 has c_x = 2600, c_z = 1800 m/s).  The
-    transpose (adjoint_step) is for kr = (1, 1, 1) only.
+    c sqrt(kr_d) (the 2D demo of Sec. 5 has c_x = 2600, c_z = 1800 m/s).
     K: bulk modulus K = rho c^2 per node (Sec. 3.1); rho: the density, a
     constant or an array [nz][ny][nx] of per-node values (variable density,
     collocated with p and v: the velocity update at a node uses dt / rho of

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
+from paper_2606_06910_gb300 import synth
 
 KR = (2600.0 ** 2 / 1800.0 ** 2, 0.7, 1.0)
 
@@ -78,3 +79,77 @@ def test_unit_factors_equal_isotropic_grid():
         out.append(st)
     for k in O.FIELDS:
         assert np.array_equal(out[0][k], out[1][k]), k
+
+
+def _aniso_adjoint_case(kr_adj=None):
+    shape = (10, 11, 12)
+    L = (2, 3, 3, 2, 2, 3)
+    h, c = 10.0, 2000.0
+    kr = (1.7, 0.6, 1.2)
+    dt = 0.35 * h / (c * np.sqrt(max(kr)))
+    rng = np.random.default_rng(19)
+    K = rng.uniform(1500, 2500, size=shape) ** 2
+    prof = O.make_profiles(shape, L, h, dt, c * np.sqrt(max(kr)), R=1e-5)
+    g = O.Grid(K, h, dt, prof, kr=kr)
+    ga = g if kr_adj is None else O.Grid(K, h, dt, prof, kr=kr_adj)
+    xs = synth.random_state(shape, L, seed=23, v_scale=dt / h, psiv_scale=1 / h,
+                            psip_scale=dt / h ** 2, dtype=np.float64)
+    ys = synth.random_state(shape, L, seed=24, dtype=np.float64)
+    x = O.State(shape)
+    y = O.State(shape)
+    for k in O.FIELDS:
+        x[k] = xs[k]
+        y[k] = ys[k]
+    fx = x.copy()
+    O.run(g, fx, 6)
+    aty = y.copy()
+    for _ in range(6):
+        O.adjoint_step(ga, O.State(shape), aty)
+    lhs = float(np.dot(fx.as_vector(), y.as_vector()))
+    rhs = float(np.dot(x.as_vector(), aty.as_vector()))
+    return lhs, rhs
+
+
+def test_anisotropic_dot_product_identity():
+    """<F x, y> = <x, F^T y> over 6 anisotropic steps with unequal CPML
+    layers: the transpose weights axis d's bracket by kr_d, also through the
+    memory variables."""
+    lhs, rhs = _aniso_adjoint_case()
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_anisotropic_dot_product_detects_unweighted_transpose():
+    """The same identity with the isotropic transpose fails: the pin sees a
+    missing kr weight."""
+    lhs, rhs = _aniso_adjoint_case(kr_adj=(1.0, 1.0, 1.0))
+    assert abs(lhs - rhs) > 1e-3 * abs(lhs)
+
+
+def test_anisotropic_gradient_matches_central_differences():
+    """dJ/dK of the anisotropic misfit against central differences of the
+    FP64 misfit at random nodes, in the slabs and near the source."""
+    shape, L, h = (14, 13, 15), (3, 3, 2, 3, 3, 2), 10.0
+    kr = (1.5, 0.8, 1.0)
+    rng = np.random.default_rng(4)
+    c_true = rng.uniform(1800, 2600, size=shape)
+    c0 = np.full(shape, 2200.0)
+    dt = 0.4 * h / (2600.0 * np.sqrt(max(kr)))
+    prof = O.make_profiles(shape, L, h, dt, 2600.0 * np.sqrt(max(kr)), R=1e-5)
+    nt = 50
+    src = (7, 6, 7)
+    wav = synth.ricker(nt, dt, 40.0)
+    rec = np.array([[4, 4, 5], [5, 9, 9], [10, 6, 4], [3, 10, 11], [11, 9, 10]])
+    dobs = O.forward_traces(O.Grid(c_true ** 2, h, dt, prof, kr=kr), nt, src, wav, rec)
+    K0 = c0 ** 2
+    _, gK, _, _ = O.misfit_gradient(O.Grid(K0, h, dt, prof, kr=kr), nt, src, wav, rec, dobs, checkpoint_every=9)
+    nodes = [tuple(int(rng.integers(0, s)) for s in shape) for _ in range(5)] + [(7, 6, 8), (0, 0, 0), (13, 12, 14)]
+    scale = np.max(np.abs(gK))
+    for node in nodes:
+        eps = 1e-4 * K0[node]
+        Kp, Km = K0.copy(), K0.copy()
+        Kp[node] += eps
+        Km[node] -= eps
+        Jp, _ = O.misfit(O.Grid(Kp, h, dt, prof, kr=kr), nt, src, wav, rec, dobs)
+        Jm, _ = O.misfit(O.Grid(Km, h, dt, prof, kr=kr), nt, src, wav, rec, dobs)
+        fd = (Jp - Jm) / (2 * eps)
+        assert abs(gK[node] - fd) <= 1e-6 * scale + 1e-5 * abs(fd), (node, gK[node], fd)
