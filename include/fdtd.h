@@ -169,9 +169,11 @@ int fdtd_set_cpml_local(fdtd_ctx *ctx, const float *vel_dev, double R, double ka
  * The stability limit becomes c_max dt / h <= 2 / (sqrt(sum_d kr_d) max_theta
  * 2 sum_l a_l sin(l theta)); EUNSTABLE (factors unchanged) if a set model
  * violates it, and fdtd_set_model checks it too.  The CPML grading keeps
- * its single c_ref.  The adjoint is not provided for kr != (1, 1, 1)
- * (fdtd_adjoint_step_n: EUNSUPPORTED).  A 2D run is ny = 1 with no y layer
- * (the zero values beyond the grid make delta_y vanish there). */
+ * its single c_ref.  fdtd_adjoint_step_n transposes the anisotropic step
+ * (axis d's bracket keeps its factor kr_d, also through the CPML memory
+ * variables); its gradients are with respect to the base modulus K = c^2.
+ * A 2D run is ny = 1 with no y layer (the zero values beyond the grid make
+ * delta_y vanish there). */
 int fdtd_set_anisotropy(fdtd_ctx *ctx, const double kr[3]);
 
 /* Staggered (Yee) form of the same system (Sec. 3.1 names both grids):

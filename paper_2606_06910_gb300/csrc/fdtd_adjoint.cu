@@ -1,11 +1,11 @@
 // Discrete adjoint of the fused step: the exact transpose of
 //   g_d = D_d p ; psiv_d' = b psiv_d + a g_d ; v_d' = v_d - dtr (kinv g_d + psiv_d')
-//   h_d = D_d v_d' ; psip_d' = b psip_d + a h_d ; p' = p - kdt sum_d (kinv h_d + psip_d')
+//   h_d = D_d v_d' ; psip_d' = b psip_d + a h_d ; p' = p - kdt sum_d kr_d (kinv h_d + psip_d')
 // (CPML terms only inside the d-slab; paper Sec. 3.1-3.2), taken assignment
 // by assignment in reverse.  With zero values beyond the grid the transpose
 // of the centred derivative is its negative, so the adjoint is again a pair
 // of radius-4 stencils, applied to pointwise-transformed adjoint fields:
-//   stage A (pressure):  q = -kdt lam_p ; lam_h_d = kinv q + a (lam_psip_d + q)
+//   stage A (pressure):  q = -kr_d kdt lam_p ; lam_h_d = kinv q + a (lam_psip_d + q)
 //                        lam_v_d -= D_d lam_h_d ; lam_psip_d <- b (lam_psip_d + q)
 //   stage B (velocity):  r = -dtr lam_v_d ; lam_g_d = kinv r + a (lam_psiv_d + r)
 //                        lam_p -= sum_d D_d lam_g_d ; lam_psiv_d <- b (lam_psiv_d + r)
@@ -31,6 +31,7 @@ struct AdjArgs {
     float c[4];
     float dtr;
     float dt_over_vs;
+    float kr[3];                  // anisotropy factors of the pressure bracket (x, y, z)
     const float *s_tape;          // bracket of this step [nshots][vol]
     const float *slab_tape[3];    // (g, psiv_old, h, psip_old) per slab node, or null
     float *gradK;                 // [nshots][vol]
@@ -49,7 +50,7 @@ __device__ __forceinline__ float lam_h(const AdjArgs &A, int d, int z, int y, in
     if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz)
         return 0.f;
     const long long o = (long long)z * g.plane + (long long)y * g.nxp + x;
-    const float q = ap[o];   // mu = kdt lam_p
+    const float q = A.kr[d] * ap[o];   // kr_d mu, mu = kdt lam_p
     const int k = axis_coord(d, z, y, x);
     if (in_slab(k, axis_len(g, d), g.lo[d], g.hi[d]))
         return A.ck[d][k] * q + A.ca[d][k] * (apsip_in[slab_index(g, d, z, y, x)] + q);
@@ -95,13 +96,14 @@ __global__ void adj_stage_a_kernel(AdjArgs A)
         const int k = axis_coord(d, z, y, x);
         if (in_slab(k, axis_len(g, d), g.lo[d], g.hi[d])) {
             const long long si = slab_index(g, d, z, y, x);
-            const float tot = psin[si] + q;
+            const float qd = A.kr[d] * q;
+            const float tot = psin[si] + qd;
             A.apsip_out[d][(long long)shot * g.slab[d] + si] = A.cb[d][k] * tot;
             if (A.gprof) {
                 const float *tp = A.slab_tape[d] + ((long long)shot * g.slab[d] + si) * 4;
                 atomicAdd(&A.gprof[(d * 3 + 0) * A.nmax + k], tot * tp[3]);
                 atomicAdd(&A.gprof[(d * 3 + 1) * A.nmax + k], tot * tp[2]);
-                atomicAdd(&A.gprof[(d * 3 + 2) * A.nmax + k], q * tp[2]);
+                atomicAdd(&A.gprof[(d * 3 + 2) * A.nmax + k], qd * tp[2]);
             }
         }
     }
@@ -226,6 +228,8 @@ cudaError_t adjoint_step(fdtd_ctx *c, const float *s_tape, float *const slab_tap
         a.c[l] = (float)(kWeights[l] / c->d.h);
     a.dtr = (float)(c->d.dt * c->vscale);
     a.dt_over_vs = (float)(c->d.dt / c->vscale);
+    for (int d = 0; d < 3; ++d)
+        a.kr[d] = (float)c->kr[d];
     a.s_tape = s_tape;
     a.gradK = c->gradK;
     a.gprof = want_prof ? c->gprof : nullptr;

@@ -3,7 +3,8 @@
 // assignment-by-assignment transpose is spelled out in fdtd_adjoint.cu):
 //
 //   stage A (transpose of the pressure update), per node:
-//     q = kdt lam_p                              (kdt = -dt K / vscale)
+//     q = kr_d kdt lam_p                         (kdt = -dt K / vscale; kr_d the
+//                                                 anisotropy factor of axis d, 1 if none)
 //     lam_h_d = q + [d-slab] ((kinv_d - 1) q + a_d (lam_psip_d + q))
 //     lam_v'_d = lam_v_d - D_d lam_h_d ;  lam_psip_d <- b_d (lam_psip_d + q)
 //     dJ/dK += -(dt / vscale) S lam_p            (S: the taped bracket)
@@ -76,6 +77,7 @@ struct FusedArgs {
     float c[4];
     float dtr;
     float dt_over_vs;
+    float kr[3];                       // anisotropy factors of the pressure bracket (x, y, z)
     const float *s_tape;               // [nshots][vol]
     float *gradK;                      // [nshots][vol]
     unsigned *err;
@@ -307,6 +309,9 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
         gq[k] = f4z();
         if (z >= 0 && row_ok) {
             hq[k] = ld4s(A.ap_in + fo + (long long)z * G.plane + rowofs);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                hq[k].v[i] *= A.kr[2];
             if (kEdge && in_slab(z, G.nz, G.lo[2], G.hi[2])) {
                 const F4 ps = ld4s(pspin[2] + slab_index(G, 2, z, gy, gx));
                 const float a = __ldg(A.ca[2] + z), kk = __ldg(A.ck[2] + z);
@@ -372,6 +377,9 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
             F4 hn = f4z();
             if (ok && zq >= 0 && zq < G.nz) {
                 hn = ld4s(S + L::PQ + ty * TX + 4 * tx);   // TMA fills zeros beyond the grid
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    hn.v[i] *= A.kr[2];
                 if (kEdge && row_ok && in_slab(zq, G.nz, G.lo[2], G.hi[2])) {
                     const long long si = slab_index(G, 2, zq, gy, gx);
                     const F4 ps = ld4s(pspin[2] + si);
@@ -432,6 +440,9 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
         constexpr int hxw = AW;
         const int hyw = ys_tile ? TX : AW;
         const bool build_h = xs_tile || ys_tile;   // CTA-uniform
+        // lam_h in shared memory carries kr_d already; the staged mu plane
+        // does not, so derivatives read from it are scaled by kr_d
+        const float kxs = xs_tile ? 1.f : A.kr[0], kys = ys_tile ? 1.f : A.kr[1];
 
         if (kEdge) {
             // ---- lam_h_x (own rows, x halo 8), lam_h_y (own columns, y halo 8)
@@ -444,6 +455,9 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                             continue;
                         const int r = v / (AW / 4), c = 4 * (v % (AW / 4));
                         F4 h = ld4s(S + L::P + (r + AH) * AW + c);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            h.v[i] *= A.kr[0];
                         const int x = x0 - AH + c, y = y0 + r;
                         if (xs_tile && x >= 0 && x < G.nx && y < G.ny && (x < G.lo[0] || x + 3 >= G.nx - G.hi[0])) {
                             const F4 ps = ld4s(pspin[0] + slab_index(G, 0, t, y, x));
@@ -458,6 +472,9 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                         const int u = v - TY * AW / 4;  // 0 .. 383
                         const int r = u / (TX / 4), c = 4 * (u % (TX / 4));
                         F4 h = ld4s(S + L::P + r * AW + c + AH);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            h.v[i] *= A.kr[1];
                         const int y = y0 - AH + r, x = x0 + c;
                         if (ys_tile && y >= 0 && y < G.ny && x < G.nxp && in_slab(y, G.ny, G.lo[1], G.hi[1])) {
                             const F4 ps = ld4s(pspin[1] + slab_index(G, 1, t, y, x));
@@ -489,7 +506,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 const F4 dh = drow(hxs + ty * hxw, 4 * tx + AH, w);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    vx.v[i] -= dh.v[i];
+                    vx.v[i] -= kxs * dh.v[i];
                     gxo.v[i] = ndtr * vx.v[i];
                 }
                 if (own_x) {
@@ -512,7 +529,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 const F4 dh = dcol(hys, hyw, ty + AH, 4 * tx, w);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    vy.v[i] -= dh.v[i];
+                    vy.v[i] -= kys * dh.v[i];
                     gyo.v[i] = ndtr * vy.v[i];
                 }
                 if (own_y) {
@@ -542,7 +559,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 const int r = yh_y - y0 + 4, c = yh_x - x0;
                 float2 vy = ld2s(S + L::VY + r * TX + c);
                 const float2 dh = dcol2(hys, hyw, yh_y - y0 + AH, c, w);
-                gh = make_float2(ndtr * (vy.x - dh.x), ndtr * (vy.y - dh.y));
+                gh = make_float2(ndtr * (vy.x - kys * dh.x), ndtr * (vy.y - kys * dh.y));
                 if (kEdge) {
                     if (ys_tile && yh_in && yh_x < G.nxp && in_slab(yh_y, G.ny, G.lo[1], G.hi[1])) {
                         const float2 ps = ld2s(psvin[1] + slab_index(G, 1, t, yh_y, yh_x));
@@ -557,7 +574,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 const int r = xh_y - y0, c = xh_x - x0 + 4;
                 float2 vx = ld2s(S + L::VX + r * GW + c);
                 const float2 dh = drow2(hxs + r * hxw, xh_x - x0 + AH, w);
-                gh = make_float2(ndtr * (vx.x - dh.x), ndtr * (vx.y - dh.y));
+                gh = make_float2(ndtr * (vx.x - kxs * dh.x), ndtr * (vx.y - kxs * dh.y));
                 if (kEdge) {
                     if (xs_tile && xh_in && xh_x >= 0 && xh_x < G.nx &&
                         (xh_x < G.lo[0] || xh_x + 1 >= G.nx - G.hi[0])) {
@@ -579,7 +596,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                     F4 pn;
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        pn.v[i] = sCx[4 * tx + AH + i] * (ps.v[i] + q.v[i]);
+                        pn.v[i] = sCx[4 * tx + AH + i] * (ps.v[i] + A.kr[0] * q.v[i]);
                     st4s(pspout[0] + si, pn);
                 }
                 if (own_y) {
@@ -589,7 +606,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                     F4 pn;
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        pn.v[i] = b * (ps.v[i] + q.v[i]);
+                        pn.v[i] = b * (ps.v[i] + A.kr[1] * q.v[i]);
                     st4s(pspout[1] + si, pn);
                 }
                 const F4 kd = ld4s(S + L::KT + ty * TX + 4 * tx);
@@ -719,6 +736,8 @@ cudaError_t adjoint_step_fused(fdtd_ctx *c, const float *s_tape)
         a.c[l] = (float)(kWeights[l] / c->d.h);
     a.dtr = (float)(c->d.dt * c->vscale);
     a.dt_over_vs = (float)(c->d.dt / c->vscale);
+    for (int d = 0; d < 3; ++d)
+        a.kr[d] = (float)c->kr[d];
     a.s_tape = s_tape;
     a.gradK = c->gradK;
     a.err = c->err;

@@ -1147,8 +1147,6 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
         return fail(c, FDTD_EINVAL, "grad_cpml needs cpml_grad at create time");
     if (c->var_rho)
         return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for constant density (rho = 1) only");
-    if (c->kr[0] != 1.0 || c->kr[1] != 1.0 || c->kr[2] != 1.0)
-        return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the isotropic system only");
     if (c->staggered)
         return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the collocated form only");
     if (c->cpml_local_set)

@@ -132,6 +132,103 @@ def test_anisotropy_errors():
     sim.set_anisotropy((1.2, 1.0, 0.8))
     sim.set_cpml(R=1e-5, c_ref=c)
     sim.step(4)
-    with pytest.raises(FdtdError) as ei:
-        sim.adjoint(4)
-    assert ei.value.status == _lib.EUNSUPPORTED
+    sim.adjoint(4)          # the transpose of the anisotropic step is provided
+    sim.sync()
+
+
+@pytest.mark.parametrize("shape,cells,zchunk,kr", [
+    ((37, 70, 75), (5, 6, 4, 7, 3, 5), 8, (1.7, 0.6, 1.2)),
+    ((60, 100, 100), (4, 4, 5, 3, 4, 4), 16, (0.8, 1.4, 2.0)),
+])
+def test_anisotropic_adjoint_state_and_gradient_match_oracle(monkeypatch, shape, cells, zchunk, kr):
+    """The fused adjoint of the anisotropic step after 5 steps against the
+    oracle's transpose, field by field, and dJ/dc, on 3 x 3 and 4 x 4 tiles
+    with ragged tails, six unequal layers and two shots (the 100 x 100 plane
+    with 16-plane chunks has CTAs that run the interior form)."""
+    monkeypatch.setenv("FDTD_ZCHUNK", str(zchunk))
+    Fdtd = _Fdtd()
+    h, c = 10.0, 2000.0
+    dt = 0.35 * h / (c * math.sqrt(max(kr)))
+    n, C, nshots = 5, 3, 2
+    rng = np.random.default_rng(33)
+    vel = rng.uniform(1500, c, size=shape).astype(np.float32)
+    c_ref = c * math.sqrt(max(kr))
+    sim = Fdtd(shape, h, dt, nshots=nshots, cpml_cells=cells, nt_max=n, checkpoint_every=C)
+    sim.set_model(torch.from_numpy(vel).cuda())
+    sim.set_anisotropy(kr)
+    sim.set_cpml(R=1e-4, c_ref=c_ref)
+    g = O.Grid(vel.astype(np.float64) ** 2, h, dt, O.make_profiles(shape, cells, h, dt, c_ref, R=1e-4), kr=kr)
+    refs = []
+    for s in range(nshots):
+        x = synth.random_state(shape, cells, seed=50 + s, **state_scales(h, dt))
+        y = synth.random_state(shape, cells, seed=60 + s)
+        for k in FIELDS:
+            sim.set(k, torch.from_numpy(x[k]).cuda(), s)
+            sim.set("adj_" + k, torch.from_numpy(y[k]).cuda(), s)
+        fwd = O.State(shape)
+        for k in FIELDS:
+            fwd[k] = x[k].astype(np.float64)
+        starts = []
+        for _ in range(n):
+            starts.append(fwd.copy())
+            O.run(g, fwd, 1)
+        adj = O.State(shape)
+        for k in FIELDS:
+            adj[k] = y[k].astype(np.float64)
+        gK = np.zeros(shape)
+        for k in range(n - 1, -1, -1):
+            O.adjoint_step(g, starts[k], adj, gK)
+        refs.append((adj, gK))
+    sim.step(n)
+    grad = torch.zeros(shape, device="cuda")
+    sim.adjoint(n, None, grad)
+    sim.sync()
+    for s in range(nshots):
+        for k in FIELDS:
+            e2, em = rel_errors(sim.get("adj_" + k, s).cpu().numpy(), refs[s][0][k])
+            assert e2 <= 1e-4 and em <= 1e-3, (s, k, e2, em)
+    gref = (refs[0][1] + refs[1][1]) * 2.0 * vel.astype(np.float64)
+    e2, em = rel_errors(grad.cpu().numpy(), gref)
+    assert e2 <= 1e-4 and em <= 1e-3, (e2, em)
+
+
+def test_anisotropic_cpml_profile_gradient_matches_oracle():
+    """dJ/d(b, a, 1/kappa) per axis and node (the node-per-thread adjoint
+    kernels) for an anisotropic misfit against the oracle."""
+    Fdtd = _Fdtd()
+    shape, cells, h, nt, C = (20, 18, 22), (3, 4, 2, 3, 4, 2), 10.0, 40, 15
+    kr = (1.6, 0.7, 1.1)
+    c_true = synth.layered_model(shape, seed=9, vmin=1800.0, vmax=2600.0, amp_cells=2.0)
+    c0 = synth.gaussian_smooth(c_true, 2.0)
+    dt = 0.4 * h / (2600.0 * math.sqrt(max(kr)))
+    c_ref = 2600.0 * math.sqrt(max(kr))
+    src = synth.shot_positions(shape, cells, 10, 1, z=cells[4] + 2)
+    rec = synth.receiver_grid(shape, cells, 3, 3, cells[4] + 1)
+    wav = synth.ricker(nt, dt, 35.0).astype(np.float32)[None, :]
+    prof = O.make_profiles(shape, cells, h, dt, c_ref, R=1e-5)
+    gt = O.Grid(c_true.astype(np.float64) ** 2, h, dt, prof, kr=kr)
+    dobs = O.forward_traces(gt, nt, tuple(src[0]), wav[0].astype(np.float64), rec)[None].astype(np.float32)
+    sim = Fdtd(shape, h, dt, cpml_cells=cells, nt_max=nt, nrec_max=len(rec), checkpoint_every=C, cpml_grad=True)
+    sim.set_model(torch.from_numpy(c0).cuda())
+    sim.set_anisotropy(kr)
+    sim.set_cpml(R=1e-5, c_ref=c_ref)
+    sim.inject(src, torch.from_numpy(wav).cuda())
+    sim.record(rec)
+    sim.step(nt)
+    d = torch.from_numpy(dobs).cuda()
+    resid = torch.empty_like(d)
+    sim.misfit(d, nt=nt, resid=resid)
+    grad = torch.zeros(shape, device="cuda")
+    gprof = torch.zeros((3, 3, max(shape)), device="cuda")
+    sim.adjoint(nt, resid, grad, gprof)
+    sim.sync()
+    g0 = O.Grid(c0.astype(np.float64) ** 2, h, dt, prof, kr=kr)
+    _, gK, gpo, _ = O.misfit_gradient(g0, nt, tuple(src[0]), wav[0].astype(np.float64), rec,
+                                      dobs[0].astype(np.float64), checkpoint_every=C, want_profiles=True)
+    gp = gprof.cpu().numpy()
+    for dd in range(3):
+        for coef in range(3):
+            e2, em = rel_errors(gp[dd, coef], gpo[dd, coef])
+            assert e2 <= 1e-3 and em <= 1e-3, (dd, coef, e2, em)
+    e2, em = rel_errors(grad.cpu().numpy(), gK * 2.0 * c0.astype(np.float64))
+    assert e2 <= 1e-4 and em <= 1e-3, (e2, em)
