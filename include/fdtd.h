@@ -123,9 +123,9 @@ const char *fdtd_last_error(const fdtd_ctx *ctx);
  * K = rho c^2).  vel_dev: float [nz][ny][nx] in m/s; rho_dev: NULL (density 1
  * everywhere) or float [nz][ny][nx], the density per node, collocated with p
  * and v (the velocity update at a node uses dt / rho of that node).  Both are
- * read during the call.  With a density the step reads one more table
- * (4 B per node, shared by the shots) and the adjoint is not provided
- * (fdtd_adjoint_step_n: EUNSUPPORTED).  Synchronises; EINVAL if a velocity or
+ * read during the call.  With a density the step and its adjoint read one
+ * more table (4 B per node, shared by the shots); the adjoint's gradient is
+ * then dJ/dc at fixed density.  Synchronises; EINVAL if a velocity or
  * density is not finite and positive; EUNSTABLE if max(c) dt / h exceeds the
  * collocated radius-4 leapfrog limit 2 / (sqrt(3) max_theta 2 sum_l a_l sin(l theta)) = 0.6672. */
 int fdtd_set_model(fdtd_ctx *ctx, const float *vel_dev, const float *rho_dev);
@@ -236,13 +236,15 @@ int fdtd_step_n(fdtd_ctx *ctx, int n);
  * the exact transpose of the forward step.  resid_dev (dev float
  * [nshots][nt_max][nrec], the misfit derivative dJ/dtrace) is injected at the
  * receivers.  grad_vel_dev (dev float [nz][ny][nx]) receives += dJ/dc summed
- * over shots (K = rho c^2; CPML coefficients held fixed).  grad_cpml_dev
+ * over shots (K = rho c^2, dJ/dc = 2 rho c dJ/dK; density, anisotropy and CPML
+ * coefficients held fixed).  grad_cpml_dev
  * (dev float [3][3][nmax], nullable; nmax = max(nx, ny, nz); [axis x,y,z]
  * [b, a, 1/kappa][node]) receives += dJ/d(profile) and needs cpml_grad at
  * create time (EINVAL otherwise).  Needs FP32 storage,
  * checkpoint_every > 0 and n equal to the current time index (ESTATE
- * otherwise), and an isotropic model without density (EUNSUPPORTED
- * otherwise).  Leaves the forward state undefined (call fdtd_reset). */
+ * otherwise), and the collocated form with the 1D CPML grading (EUNSUPPORTED
+ * for the staggered form or fdtd_set_cpml_local).  Leaves the forward state
+ * undefined (call fdtd_reset). */
 int fdtd_adjoint_step_n(fdtd_ctx *ctx, int n, const float *resid_dev,
                         float *grad_vel_dev, float *grad_cpml_dev);
 

@@ -32,6 +32,7 @@ struct AdjArgs {
     float dtr;
     float dt_over_vs;
     float kr[3];                  // anisotropy factors of the pressure bracket (x, y, z)
+    const float *nbr;             // density: -dtr / rho per node [vol], or null (rho = 1)
     const float *s_tape;          // bracket of this step [nshots][vol]
     const float *slab_tape[3];    // (g, psiv_old, h, psip_old) per slab node, or null
     float *gradK;                 // [nshots][vol]
@@ -64,7 +65,7 @@ __device__ __forceinline__ float lam_g(const AdjArgs &A, int d, int z, int y, in
     if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz)
         return 0.f;
     const long long o = (long long)z * g.plane + (long long)y * g.nxp + x;
-    const float r = -A.dtr * av[o];
+    const float r = (A.nbr ? A.nbr[o] : -A.dtr) * av[o];
     const int k = axis_coord(d, z, y, x);
     if (in_slab(k, axis_len(g, d), g.lo[d], g.hi[d]))
         return A.ck[d][k] * r + A.ca[d][k] * (apsiv_in[slab_index(g, d, z, y, x)] + r);
@@ -131,7 +132,7 @@ __global__ void adj_stage_b_kernel(AdjArgs A)
         const int k = axis_coord(d, z, y, x);
         if (in_slab(k, axis_len(g, d), g.lo[d], g.hi[d])) {
             const long long si = slab_index(g, d, z, y, x);
-            const float r = -A.dtr * av[o];
+            const float r = (A.nbr ? A.nbr[o] : -A.dtr) * av[o];
             const float tot = psin[si] + r;
             A.apsiv_out[d][(long long)shot * g.slab[d] + si] = A.cb[d][k] * tot;
             if (A.gprof) {
@@ -158,8 +159,10 @@ __global__ void adj_inject_kernel(float *ap, const float *kdt, Geom g, const int
     atomicAdd(&ap[(long long)shot * g.vol + o], kdt[o] * r);   // mu = kdt lam_p
 }
 
-__global__ void grad_vel_kernel(const float *gradK, const float *kdt, Geom g, int nshots, double vs_over_dt,
-                                float *grad_vel)
+// dJ/dc = 2 rho c dJ/dK with K = rho c^2 (rho fixed): -kdt vs / dt = K, and
+// with a density rho = -dt vs / nbr (nbr = -dt vs / rho), else rho = 1.
+__global__ void grad_vel_kernel(const float *gradK, const float *kdt, const float *nbr, Geom g, int nshots,
+                                double vs_over_dt, double dt_vs, float *grad_vel)
 {
     const long long n = (long long)g.nz * g.ny * g.nx;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -170,8 +173,10 @@ __global__ void grad_vel_kernel(const float *gradK, const float *kdt, Geom g, in
         double acc = 0.0;
         for (int s = 0; s < nshots; ++s)
             acc += gradK[(long long)s * g.vol + o];
-        const double c = sqrt(-(double)kdt[o] * vs_over_dt);   // K = rho c^2, rho = 1
-        grad_vel[i] += (float)(2.0 * c * acc);
+        const double K = -(double)kdt[o] * vs_over_dt;
+        const double rho = nbr ? -dt_vs / (double)nbr[o] : 1.0;
+        const double c = sqrt(K / rho);
+        grad_vel[i] += (float)(2.0 * rho * c * acc);
     }
 }
 
@@ -200,7 +205,8 @@ cudaError_t launch_adj_inject(const fdtd_ctx *c, const float *resid, int n)
 
 cudaError_t launch_grad_vel(const fdtd_ctx *c, float *grad_vel)
 {
-    grad_vel_kernel<<<1216, 256, 0, c->stream>>>(c->gradK, c->kdt, c->g, c->d.nshots, c->vscale / c->d.dt, grad_vel);
+    grad_vel_kernel<<<1216, 256, 0, c->stream>>>(c->gradK, c->kdt, c->var_rho ? c->nbr : nullptr, c->g,
+                                                 c->d.nshots, c->vscale / c->d.dt, c->d.dt * c->vscale, grad_vel);
     return cudaGetLastError();
 }
 
@@ -230,6 +236,7 @@ cudaError_t adjoint_step(fdtd_ctx *c, const float *s_tape, float *const slab_tap
     a.dt_over_vs = (float)(c->d.dt / c->vscale);
     for (int d = 0; d < 3; ++d)
         a.kr[d] = (float)c->kr[d];
+    a.nbr = c->var_rho ? c->nbr : nullptr;
     a.s_tape = s_tape;
     a.gradK = c->gradK;
     a.gprof = want_prof ? c->gprof : nullptr;

@@ -9,7 +9,7 @@
 //     lam_v'_d = lam_v_d - D_d lam_h_d ;  lam_psip_d <- b_d (lam_psip_d + q)
 //     dJ/dK += -(dt / vscale) S lam_p            (S: the taped bracket)
 //   stage B (transpose of the velocity update), per node:
-//     r_d = -dtr lam_v'_d
+//     r_d = -dtr lam_v'_d                        (-dtr / rho with a density)
 //     lam_g_d = r_d + [d-slab] ((kinv_d - 1) r_d + a_d (lam_psiv_d + r_d))
 //     lam_p' = lam_p - sum_d D_d lam_g_d ;  lam_psiv_d <- b_d (lam_psiv_d + r_d)
 //
@@ -78,6 +78,7 @@ struct FusedArgs {
     float dtr;
     float dt_over_vs;
     float kr[3];                       // anisotropy factors of the pressure bracket (x, y, z)
+    const float *nbr;                  // density: -dtr / rho per node [vol] (the forward's table)
     const float *s_tape;               // [nshots][vol]
     float *gradK;                      // [nshots][vol]
     unsigned *err;
@@ -206,7 +207,8 @@ __device__ __forceinline__ void st_own(float *p, const F4 &v, int nv)
 // and the z range with 8 planes either side lie inside the grid and outside
 // every CPML slab; then lam_h = mu, and the derivatives of stage A read the
 // staged mu plane directly.  kEdge = true forms lam_h in shared memory first.
-template <bool kEdge>
+// kRho: the velocity transpose takes -dtr / rho per node from A.nbr.
+template <bool kEdge, bool kRho>
 __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMap &mPq, const CUtensorMap &mVX,
                                          const CUtensorMap &mVY, const CUtensorMap &mVZ, const CUtensorMap &mK,
                                          const FusedArgs &A, int z0, int z1, float *sm)
@@ -403,10 +405,13 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
             if (ok && zv >= 0 && zv < G.nz) {
                 const F4 dh = dq(hq, w);
                 F4 vz = ld4s(S + L::VZ + ty * TX + 4 * tx);
+                F4 fz = F4{{ndtr, ndtr, ndtr, ndtr}};
+                if (kRho)
+                    fz = row_ok ? Io<float>::ldg4(A.nbr + (long long)zv * G.plane + rowofs) : f4z();
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     vz.v[i] -= dh.v[i];
-                    gn.v[i] = ndtr * vz.v[i];
+                    gn.v[i] = fz.v[i] * vz.v[i];
                 }
                 const bool owned = zv >= z0 && zv < z1;
                 if (owned && row_ok)
@@ -501,13 +506,16 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
         float2 gh = make_float2(0.f, 0.f);
         if (ok && active) {
             const long long o = fo + (long long)t * G.plane + rowofs;
+            F4 fo4 = F4{{ndtr, ndtr, ndtr, ndtr}};
+            if (kRho)
+                fo4 = row_ok ? Io<float>::ldg4(A.nbr + (long long)t * G.plane + rowofs) : f4z();
             {
                 F4 vx = ld4s(S + L::VX + ty * GW + 4 * tx + 4);
                 const F4 dh = drow(hxs + ty * hxw, 4 * tx + AH, w);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     vx.v[i] -= kxs * dh.v[i];
-                    gxo.v[i] = ndtr * vx.v[i];
+                    gxo.v[i] = fo4.v[i] * vx.v[i];
                 }
                 if (own_x) {
                     const long long si = slab_index(G, 0, t, gy, gx);
@@ -530,7 +538,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     vy.v[i] -= kys * dh.v[i];
-                    gyo.v[i] = ndtr * vy.v[i];
+                    gyo.v[i] = fo4.v[i] * vy.v[i];
                 }
                 if (own_y) {
                     const long long si = slab_index(G, 1, t, gy, gx);
@@ -559,7 +567,13 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 const int r = yh_y - y0 + 4, c = yh_x - x0;
                 float2 vy = ld2s(S + L::VY + r * TX + c);
                 const float2 dh = dcol2(hys, hyw, yh_y - y0 + AH, c, w);
-                gh = make_float2(ndtr * (vy.x - kys * dh.x), ndtr * (vy.y - kys * dh.y));
+                float2 fh = make_float2(ndtr, ndtr);
+                if (kRho)
+                    fh = (yh_in && yh_x < G.nxp)
+                             ? __ldg(reinterpret_cast<const float2 *>(A.nbr + (long long)t * G.plane +
+                                                                       (long long)yh_y * G.nxp + yh_x))
+                             : make_float2(0.f, 0.f);
+                gh = make_float2(fh.x * (vy.x - kys * dh.x), fh.y * (vy.y - kys * dh.y));
                 if (kEdge) {
                     if (ys_tile && yh_in && yh_x < G.nxp && in_slab(yh_y, G.ny, G.lo[1], G.hi[1])) {
                         const float2 ps = ld2s(psvin[1] + slab_index(G, 1, t, yh_y, yh_x));
@@ -574,7 +588,13 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 const int r = xh_y - y0, c = xh_x - x0 + 4;
                 float2 vx = ld2s(S + L::VX + r * GW + c);
                 const float2 dh = drow2(hxs + r * hxw, xh_x - x0 + AH, w);
-                gh = make_float2(ndtr * (vx.x - kxs * dh.x), ndtr * (vx.y - kxs * dh.y));
+                float2 fh = make_float2(ndtr, ndtr);
+                if (kRho)
+                    fh = (xh_in && xh_x >= 0 && xh_x < G.nxp)
+                             ? __ldg(reinterpret_cast<const float2 *>(A.nbr + (long long)t * G.plane +
+                                                                       (long long)xh_y * G.nxp + xh_x))
+                             : make_float2(0.f, 0.f);
+                gh = make_float2(fh.x * (vx.x - kxs * dh.x), fh.y * (vx.y - kxs * dh.y));
                 if (kEdge) {
                     if (xs_tile && xh_in && xh_x >= 0 && xh_x < G.nx &&
                         (xh_x < G.lo[0] || xh_x + 1 >= G.nx - G.hi[0])) {
@@ -665,6 +685,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
     }
 }
 
+template <bool kRho>
 __global__ void __launch_bounds__(NTHREADS, 2)
     adj_fused_kernel(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mPq,
                      const __grid_constant__ CUtensorMap mVX, const __grid_constant__ CUtensorMap mVY,
@@ -680,9 +701,9 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     const bool interior = x0 - AH >= G.lo[0] && x0 + TX + AH <= G.nx - G.hi[0] && y0 - AH >= G.lo[1] &&
                           y0 + TY + AH <= G.ny - G.hi[1] && z0 - 8 >= G.lo[2] && z1 + 8 <= G.nz - G.hi[2];
     if (interior)
-        adj_body<false>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
+        adj_body<false, kRho>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
     else
-        adj_body<true>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
+        adj_body<true, kRho>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
 }
 
 }  // namespace
@@ -693,8 +714,11 @@ cudaError_t adjoint_step_fused(fdtd_ctx *c, const float *s_tape)
 {
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e =
-            cudaFuncSetAttribute(adj_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FusedLayout::BYTES);
+        cudaError_t e = cudaFuncSetAttribute(adj_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             FusedLayout::BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(adj_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     FusedLayout::BYTES);
         if (e != cudaSuccess)
             return e;
         attr_done = true;
@@ -738,12 +762,18 @@ cudaError_t adjoint_step_fused(fdtd_ctx *c, const float *s_tape)
     a.dt_over_vs = (float)(c->d.dt / c->vscale);
     for (int d = 0; d < 3; ++d)
         a.kr[d] = (float)c->kr[d];
+    a.nbr = c->var_rho ? c->nbr : nullptr;
     a.s_tape = s_tape;
     a.gradK = c->gradK;
     a.err = c->err;
     dim3 grid(c->tiles_x * c->tiles_y, adj_chunks(a), c->d.nshots);
     const CUtensorMap *m = c->amaps[s];
-    adj_fused_kernel<<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3], m[4], c->mapK, a);
+    if (a.nbr)
+        adj_fused_kernel<true><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3], m[4],
+                                                                                  c->mapK, a);
+    else
+        adj_fused_kernel<false><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3], m[4],
+                                                                                   c->mapK, a);
     const cudaError_t e = cudaGetLastError();
     c->aset ^= 1;
     c->ap = c->apb[c->aset];

@@ -1145,8 +1145,6 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
         return fail(c, FDTD_ESTATE, "n must equal the current time index (%d) and be <= nt_max", c->t);
     if (grad_cpml && !c->d.cpml_grad)
         return fail(c, FDTD_EINVAL, "grad_cpml needs cpml_grad at create time");
-    if (c->var_rho)
-        return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for constant density (rho = 1) only");
     if (c->staggered)
         return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the collocated form only");
     if (c->cpml_local_set)
