@@ -277,7 +277,9 @@ static void og_deriv_transpose_acc(const og_grid *g, const double *y, int axis, 
  * (CPML terms only inside the d-slab; kr_d = 1 unless anisotropic), is
  * transposed assignment by assignment in reverse order.  The source term is a
  * constant and has no adjoint.
- * Collocated form with 1D profiles only (g->staggered = 0, bn = an = NULL).
+ * Collocated form (g->staggered = 0); with the local grading (bn, an) the
+ * per-node coefficients are transposed the same way, and gprof, which is
+ * per axis and node index, is for the 1D profiles only.
  */
 void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
                      double *gradK, double *gprof, long nmax)
@@ -338,13 +340,13 @@ void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
                     double q = g->kr[d] * q0;         /* adjoint of axis d's bracket */
                     if (g->slab[d][k]) {
                         double lpsi = adj->psip[d][i] + q;   /* total adjoint of psip_d' */
-                        lam_h[d][i] = g->kinv[d][k] * q + g->a[d][k] * lpsi;
+                        lam_h[d][i] = g->kinv[d][k] * q + og_a(g, d, i, k) * lpsi;
                         if (gprof) {
                             gprof[(d * 3 + 0) * nmax + k] += lpsi * fwd->psip[d][i];
                             gprof[(d * 3 + 1) * nmax + k] += lpsi * h_d[d][i];
                             gprof[(d * 3 + 2) * nmax + k] += q * h_d[d][i];
                         }
-                        adj->psip[d][i] = g->b[d][k] * lpsi;
+                        adj->psip[d][i] = og_b(g, d, i, k) * lpsi;
                     } else {
                         lam_h[d][i] = q;
                     }
@@ -365,13 +367,13 @@ void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
                     double r = -g->dt / og_rho(g, i) * adj->v[d][i];
                     if (g->slab[d][k]) {
                         double lpsi = adj->psiv[d][i] + r;
-                        lam_g[d][i] = g->kinv[d][k] * r + g->a[d][k] * lpsi;
+                        lam_g[d][i] = g->kinv[d][k] * r + og_a(g, d, i, k) * lpsi;
                         if (gprof) {
                             gprof[(d * 3 + 0) * nmax + k] += lpsi * fwd->psiv[d][i];
                             gprof[(d * 3 + 1) * nmax + k] += lpsi * g_d[d][i];
                             gprof[(d * 3 + 2) * nmax + k] += r * g_d[d][i];
                         }
-                        adj->psiv[d][i] = g->b[d][k] * lpsi;
+                        adj->psiv[d][i] = og_b(g, d, i, k) * lpsi;
                     } else {
                         lam_g[d][i] = r;
                     }
