@@ -156,8 +156,9 @@ int fdtd_set_cpml(fdtd_ctx *ctx, double R, double kappa_max, double alpha_frac,
  * previous grading; fdtd_set_cpml or fdtd_set_cpml_ska replace it in turn.
  * EINVAL for parameters as in fdtd_set_cpml or a slab velocity that is not
  * finite and positive; EUNSUPPORTED with 16-bit storage or the staggered
- * form, and the adjoint is not provided (fdtd_adjoint_step_n: EUNSUPPORTED).
- * Synchronises. */
+ * form.  fdtd_adjoint_step_n transposes the per-node coefficients (its dJ/dc
+ * holds them fixed); the CPML-profile gradient, which is per axis and node
+ * index, is not provided with them (grad_cpml: EUNSUPPORTED).  Synchronises. */
 int fdtd_set_cpml_local(fdtd_ctx *ctx, const float *vel_dev, double R, double kappa_max,
                         double alpha_frac, int q);
 
@@ -242,8 +243,8 @@ int fdtd_step_n(fdtd_ctx *ctx, int n);
  * [b, a, 1/kappa][node]) receives += dJ/d(profile) and needs cpml_grad at
  * create time (EINVAL otherwise).  Needs FP32 storage,
  * checkpoint_every > 0 and n equal to the current time index (ESTATE
- * otherwise), and the collocated form with the 1D CPML grading (EUNSUPPORTED
- * for the staggered form or fdtd_set_cpml_local).  Leaves the forward state
+ * otherwise), and the collocated form (EUNSUPPORTED for the staggered form,
+ * and for grad_cpml with fdtd_set_cpml_local).  Leaves the forward state
  * undefined (call fdtd_reset). */
 int fdtd_adjoint_step_n(fdtd_ctx *ctx, int n, const float *resid_dev,
                         float *grad_vel_dev, float *grad_cpml_dev);

@@ -79,6 +79,7 @@ struct FusedArgs {
     float dt_over_vs;
     float kr[3];                       // anisotropy factors of the pressure bracket (x, y, z)
     const float *nbr;                  // density: -dtr / rho per node [vol] (the forward's table)
+    const float *lb[3], *la[3];        // local grading: b, a per slab node (slab layout), or null
     const float *s_tape;               // [nshots][vol]
     float *gradK;                      // [nshots][vol]
     unsigned *err;
@@ -183,6 +184,11 @@ __device__ __forceinline__ F4 dq(const F4 *q, const float *w)
     return r;
 }
 
+__device__ __forceinline__ F4 f4s(float a) { return F4{{a, a, a, a}}; }
+// per-node coefficients of 4 nodes (local grading tables, read-only)
+__device__ __forceinline__ F4 ldc4(const float *p) { return Io<float>::ldg4(p); }
+__device__ __forceinline__ float2 ldc2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+
 // lam + ((kinv - 1) lam + a (psi + lam)): the CPML bracket's transpose
 __device__ __forceinline__ float corr1(float lam, float psi, float a, float k)
 {
@@ -208,7 +214,8 @@ __device__ __forceinline__ void st_own(float *p, const F4 &v, int nv)
 // every CPML slab; then lam_h = mu, and the derivatives of stage A read the
 // staged mu plane directly.  kEdge = true forms lam_h in shared memory first.
 // kRho: the velocity transpose takes -dtr / rho per node from A.nbr.
-template <bool kEdge, bool kRho>
+// kLocal: b and a of every slab node come from A.lb, A.la (local grading).
+template <bool kEdge, bool kRho, bool kLocal>
 __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMap &mPq, const CUtensorMap &mVX,
                                          const CUtensorMap &mVY, const CUtensorMap &mVZ, const CUtensorMap &mK,
                                          const FusedArgs &A, int z0, int z1, float *sm)
@@ -315,11 +322,13 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
             for (int i = 0; i < 4; ++i)
                 hq[k].v[i] *= A.kr[2];
             if (kEdge && in_slab(z, G.nz, G.lo[2], G.hi[2])) {
-                const F4 ps = ld4s(pspin[2] + slab_index(G, 2, z, gy, gx));
-                const float a = __ldg(A.ca[2] + z), kk = __ldg(A.ck[2] + z);
+                const long long si = slab_index(G, 2, z, gy, gx);
+                const F4 ps = ld4s(pspin[2] + si);
+                const F4 a = kLocal ? ldc4(A.la[2] + si) : f4s(__ldg(A.ca[2] + z));
+                const float kk = __ldg(A.ck[2] + z);
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    hq[k].v[i] = corr1(hq[k].v[i], ps.v[i], a, kk);
+                    hq[k].v[i] = corr1(hq[k].v[i], ps.v[i], a.v[i], kk);
             }
         }
     }
@@ -385,18 +394,19 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 if (kEdge && row_ok && in_slab(zq, G.nz, G.lo[2], G.hi[2])) {
                     const long long si = slab_index(G, 2, zq, gy, gx);
                     const F4 ps = ld4s(pspin[2] + si);
-                    const float a = __ldg(A.ca[2] + zq), kk = __ldg(A.ck[2] + zq);
+                    const F4 a = kLocal ? ldc4(A.la[2] + si) : f4s(__ldg(A.ca[2] + zq));
+                    const float kk = __ldg(A.ck[2] + zq);
                     if (zq >= z0 && zq < z1) {
-                        const float b = __ldg(A.cb[2] + zq);
+                        const F4 b = kLocal ? ldc4(A.lb[2] + si) : f4s(__ldg(A.cb[2] + zq));
                         F4 pn;
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            pn.v[i] = b * (ps.v[i] + hn.v[i]);
+                            pn.v[i] = b.v[i] * (ps.v[i] + hn.v[i]);
                         st4s(pspout[2] + si, pn);
                     }
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        hn.v[i] = corr1(hn.v[i], ps.v[i], a, kk);
+                        hn.v[i] = corr1(hn.v[i], ps.v[i], a.v[i], kk);
                 }
             }
             hq[8] = hn;
@@ -420,17 +430,18 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                     const long long si = slab_index(G, 2, zv, gy, gx);
                     const F4 ps = ld4s(psvin[2] + si);
                     if (owned) {
-                        const float b = __ldg(A.cb[2] + zv);
+                        const F4 b = kLocal ? ldc4(A.lb[2] + si) : f4s(__ldg(A.cb[2] + zv));
                         F4 pn;
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            pn.v[i] = b * (ps.v[i] + gn.v[i]);
+                            pn.v[i] = b.v[i] * (ps.v[i] + gn.v[i]);
                         st4s(psvout[2] + si, pn);
                     }
-                    const float a = __ldg(A.ca[2] + zv), kk = __ldg(A.ck[2] + zv);
+                    const F4 a = kLocal ? ldc4(A.la[2] + si) : f4s(__ldg(A.ca[2] + zv));
+                    const float kk = __ldg(A.ck[2] + zv);
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        gn.v[i] = corr1(gn.v[i], ps.v[i], a, kk);
+                        gn.v[i] = corr1(gn.v[i], ps.v[i], a.v[i], kk);
                 }
             }
             gq[8] = gn;
@@ -465,10 +476,13 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                             h.v[i] *= A.kr[0];
                         const int x = x0 - AH + c, y = y0 + r;
                         if (xs_tile && x >= 0 && x < G.nx && y < G.ny && (x < G.lo[0] || x + 3 >= G.nx - G.hi[0])) {
-                            const F4 ps = ld4s(pspin[0] + slab_index(G, 0, t, y, x));
+                            const long long si = slab_index(G, 0, t, y, x);
+                            const F4 ps = ld4s(pspin[0] + si);
+                            const F4 a = kLocal ? ldc4(A.la[0] + si)
+                                                : F4{{sCx[AW + c], sCx[AW + c + 1], sCx[AW + c + 2], sCx[AW + c + 3]}};
 #pragma unroll
                             for (int i = 0; i < 4; ++i)
-                                h.v[i] = corr1(h.v[i], ps.v[i], sCx[AW + c + i], sCx[2 * AW + c + i]);
+                                h.v[i] = corr1(h.v[i], ps.v[i], a.v[i], sCx[2 * AW + c + i]);
                         }
                         st4s(HX + r * AW + c, h);
                     } else {
@@ -482,10 +496,12 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                             h.v[i] *= A.kr[1];
                         const int y = y0 - AH + r, x = x0 + c;
                         if (ys_tile && y >= 0 && y < G.ny && x < G.nxp && in_slab(y, G.ny, G.lo[1], G.hi[1])) {
-                            const F4 ps = ld4s(pspin[1] + slab_index(G, 1, t, y, x));
+                            const long long si = slab_index(G, 1, t, y, x);
+                            const F4 ps = ld4s(pspin[1] + si);
+                            const F4 a = kLocal ? ldc4(A.la[1] + si) : f4s(sCy[AW + r]);
 #pragma unroll
                             for (int i = 0; i < 4; ++i)
-                                h.v[i] = corr1(h.v[i], ps.v[i], sCy[AW + r], sCy[2 * AW + r]);
+                                h.v[i] = corr1(h.v[i], ps.v[i], a.v[i], sCy[2 * AW + r]);
                         }
                         st4s(HY + r * TX + c, h);
                     }
@@ -520,12 +536,16 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 if (own_x) {
                     const long long si = slab_index(G, 0, t, gy, gx);
                     const F4 ps = ld4s(psvin[0] + si);
+                    const int c0 = 4 * tx + AH;
+                    const F4 b = kLocal ? ldc4(A.lb[0] + si) : F4{{sCx[c0], sCx[c0 + 1], sCx[c0 + 2], sCx[c0 + 3]}};
+                    const F4 a = kLocal ? ldc4(A.la[0] + si)
+                                        : F4{{sCx[AW + c0], sCx[AW + c0 + 1], sCx[AW + c0 + 2], sCx[AW + c0 + 3]}};
                     F4 pn;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const int cc = 4 * tx + AH + i;
-                        pn.v[i] = sCx[cc] * (ps.v[i] + gxo.v[i]);
-                        gxo.v[i] = corr1(gxo.v[i], ps.v[i], sCx[AW + cc], sCx[2 * AW + cc]);
+                        const int cc = c0 + i;
+                        pn.v[i] = b.v[i] * (ps.v[i] + gxo.v[i]);
+                        gxo.v[i] = corr1(gxo.v[i], ps.v[i], a.v[i], sCx[2 * AW + cc]);
                     }
                     st4s(psvout[0] + si, pn);
                 }
@@ -543,12 +563,14 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 if (own_y) {
                     const long long si = slab_index(G, 1, t, gy, gx);
                     const F4 ps = ld4s(psvin[1] + si);
-                    const float b = sCy[ty + AH], a = sCy[AW + ty + AH], kk = sCy[2 * AW + ty + AH];
+                    const F4 b = kLocal ? ldc4(A.lb[1] + si) : f4s(sCy[ty + AH]);
+                    const F4 a = kLocal ? ldc4(A.la[1] + si) : f4s(sCy[AW + ty + AH]);
+                    const float kk = sCy[2 * AW + ty + AH];
                     F4 pn;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        pn.v[i] = b * (ps.v[i] + gyo.v[i]);
-                        gyo.v[i] = corr1(gyo.v[i], ps.v[i], a, kk);
+                        pn.v[i] = b.v[i] * (ps.v[i] + gyo.v[i]);
+                        gyo.v[i] = corr1(gyo.v[i], ps.v[i], a.v[i], kk);
                     }
                     st4s(psvout[1] + si, pn);
                 }
@@ -576,10 +598,12 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 gh = make_float2(fh.x * (vy.x - kys * dh.x), fh.y * (vy.y - kys * dh.y));
                 if (kEdge) {
                     if (ys_tile && yh_in && yh_x < G.nxp && in_slab(yh_y, G.ny, G.lo[1], G.hi[1])) {
-                        const float2 ps = ld2s(psvin[1] + slab_index(G, 1, t, yh_y, yh_x));
-                        const float a = sCy[AW + r + 4], kk = sCy[2 * AW + r + 4];
-                        gh.x = corr1(gh.x, ps.x, a, kk);
-                        gh.y = corr1(gh.y, ps.y, a, kk);
+                        const long long ih = slab_index(G, 1, t, yh_y, yh_x);
+                        const float2 ps = ld2s(psvin[1] + ih);
+                        const float2 a = kLocal ? ldc2(A.la[1] + ih) : make_float2(sCy[AW + r + 4], sCy[AW + r + 4]);
+                        const float kk = sCy[2 * AW + r + 4];
+                        gh.x = corr1(gh.x, ps.x, a.x, kk);
+                        gh.y = corr1(gh.y, ps.y, a.y, kk);
                     }
                     gh.x = (yh_in && yh_x < G.nx) ? gh.x : 0.f;
                     gh.y = (yh_in && yh_x + 1 < G.nx) ? gh.y : 0.f;
@@ -598,10 +622,12 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 if (kEdge) {
                     if (xs_tile && xh_in && xh_x >= 0 && xh_x < G.nx &&
                         (xh_x < G.lo[0] || xh_x + 1 >= G.nx - G.hi[0])) {
-                        const float2 ps = ld2s(psvin[0] + slab_index(G, 0, t, xh_y, xh_x));
+                        const long long ih = slab_index(G, 0, t, xh_y, xh_x);
+                        const float2 ps = ld2s(psvin[0] + ih);
                         const int cc = xh_x - x0 + AH;
-                        gh.x = corr1(gh.x, ps.x, sCx[AW + cc], sCx[2 * AW + cc]);
-                        gh.y = corr1(gh.y, ps.y, sCx[AW + cc + 1], sCx[2 * AW + cc + 1]);
+                        const float2 a = kLocal ? ldc2(A.la[0] + ih) : make_float2(sCx[AW + cc], sCx[AW + cc + 1]);
+                        gh.x = corr1(gh.x, ps.x, a.x, sCx[2 * AW + cc]);
+                        gh.y = corr1(gh.y, ps.y, a.y, sCx[2 * AW + cc + 1]);
                     }
                     gh.x = (xh_in && xh_x >= 0 && xh_x < G.nx) ? gh.x : 0.f;
                     gh.y = (xh_in && xh_x + 1 >= 0 && xh_x + 1 < G.nx) ? gh.y : 0.f;
@@ -613,20 +639,22 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 if (own_x) {
                     const long long si = slab_index(G, 0, t, gy, gx);
                     const F4 ps = ld4s(pspin[0] + si);
+                    const int c0 = 4 * tx + AH;
+                    const F4 b = kLocal ? ldc4(A.lb[0] + si) : F4{{sCx[c0], sCx[c0 + 1], sCx[c0 + 2], sCx[c0 + 3]}};
                     F4 pn;
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        pn.v[i] = sCx[4 * tx + AH + i] * (ps.v[i] + A.kr[0] * q.v[i]);
+                        pn.v[i] = b.v[i] * (ps.v[i] + A.kr[0] * q.v[i]);
                     st4s(pspout[0] + si, pn);
                 }
                 if (own_y) {
                     const long long si = slab_index(G, 1, t, gy, gx);
                     const F4 ps = ld4s(pspin[1] + si);
-                    const float b = sCy[ty + AH];
+                    const F4 b = kLocal ? ldc4(A.lb[1] + si) : f4s(sCy[ty + AH]);
                     F4 pn;
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        pn.v[i] = b * (ps.v[i] + A.kr[1] * q.v[i]);
+                        pn.v[i] = b.v[i] * (ps.v[i] + A.kr[1] * q.v[i]);
                     st4s(pspout[1] + si, pn);
                 }
                 const F4 kd = ld4s(S + L::KT + ty * TX + 4 * tx);
@@ -685,7 +713,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
     }
 }
 
-template <bool kRho>
+template <bool kRho, bool kLocal>
 __global__ void __launch_bounds__(NTHREADS, 2)
     adj_fused_kernel(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mPq,
                      const __grid_constant__ CUtensorMap mVX, const __grid_constant__ CUtensorMap mVY,
@@ -701,9 +729,9 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     const bool interior = x0 - AH >= G.lo[0] && x0 + TX + AH <= G.nx - G.hi[0] && y0 - AH >= G.lo[1] &&
                           y0 + TY + AH <= G.ny - G.hi[1] && z0 - 8 >= G.lo[2] && z1 + 8 <= G.nz - G.hi[2];
     if (interior)
-        adj_body<false, kRho>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
+        adj_body<false, kRho, false>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
     else
-        adj_body<true, kRho>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
+        adj_body<true, kRho, kLocal>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
 }
 
 }  // namespace
@@ -714,11 +742,11 @@ cudaError_t adjoint_step_fused(fdtd_ctx *c, const float *s_tape)
 {
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(adj_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             FusedLayout::BYTES);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(adj_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     FusedLayout::BYTES);
+        const void *kern[4] = {(const void *)adj_fused_kernel<false, false>, (const void *)adj_fused_kernel<true, false>,
+                               (const void *)adj_fused_kernel<false, true>, (const void *)adj_fused_kernel<true, true>};
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            e = cudaFuncSetAttribute(kern[k], cudaFuncAttributeMaxDynamicSharedMemorySize, FusedLayout::BYTES);
         if (e != cudaSuccess)
             return e;
         attr_done = true;
@@ -763,17 +791,28 @@ cudaError_t adjoint_step_fused(fdtd_ctx *c, const float *s_tape)
     for (int d = 0; d < 3; ++d)
         a.kr[d] = (float)c->kr[d];
     a.nbr = c->var_rho ? c->nbr : nullptr;
+    for (int d = 0; d < 3; ++d) {
+        a.lb[d] = c->cpml_local_set ? c->lcoef[d][0] : nullptr;
+        a.la[d] = c->cpml_local_set ? c->lcoef[d][1] : nullptr;
+    }
     a.s_tape = s_tape;
     a.gradK = c->gradK;
     a.err = c->err;
     dim3 grid(c->tiles_x * c->tiles_y, adj_chunks(a), c->d.nshots);
     const CUtensorMap *m = c->amaps[s];
-    if (a.nbr)
-        adj_fused_kernel<true><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3], m[4],
-                                                                                  c->mapK, a);
+    const bool loc = a.lb[0] != nullptr;
+    if (a.nbr && loc)
+        adj_fused_kernel<true, true><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3], m[4],
+                                                                                        c->mapK, a);
+    else if (a.nbr)
+        adj_fused_kernel<true, false><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3],
+                                                                                         m[4], c->mapK, a);
+    else if (loc)
+        adj_fused_kernel<false, true><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3],
+                                                                                         m[4], c->mapK, a);
     else
-        adj_fused_kernel<false><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3], m[4],
-                                                                                   c->mapK, a);
+        adj_fused_kernel<false, false><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3],
+                                                                                          m[4], c->mapK, a);
     const cudaError_t e = cudaGetLastError();
     c->aset ^= 1;
     c->ap = c->apb[c->aset];

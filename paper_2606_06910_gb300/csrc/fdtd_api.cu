@@ -1147,8 +1147,8 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
         return fail(c, FDTD_EINVAL, "grad_cpml needs cpml_grad at create time");
     if (c->staggered)
         return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the collocated form only");
-    if (c->cpml_local_set)
-        return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the 1D CPML grading only");
+    if (c->cpml_local_set && grad_cpml)
+        return fail(c, FDTD_EUNSUPPORTED, "the CPML-profile gradient is for the 1D grading (per axis and node)");
     const bool want_prof = grad_cpml != nullptr;
     const int nmax = nmax_of(c->g);
     CUDA_TRY(c, cudaMemsetAsync(c->gradK, 0, (size_t)c->d.nshots * c->g.vol * 4, c->stream));

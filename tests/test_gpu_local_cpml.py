@@ -221,7 +221,7 @@ def test_local_grading_restrictions():
     plain = Fdtd(shape, h, 0.4 * h / c, cpml_cells=3, nt_max=4)
     plain.set_model(vel)
     assert status(lambda: plain.set_cpml_local(vel)) == _lib.ESTATE
-    sim = Fdtd(shape, h, 0.4 * h / c, cpml_cells=3, nt_max=4, checkpoint_every=2, cpml_local=True)
+    sim = Fdtd(shape, h, 0.4 * h / c, cpml_cells=3, nt_max=4, checkpoint_every=2, cpml_local=True, cpml_grad=True)
     assert status(lambda: sim.set_cpml_local(vel)) == _lib.ESTATE          # no model yet
     sim.set_model(vel)
     bad = vel.clone()
@@ -230,7 +230,10 @@ def test_local_grading_restrictions():
     sim.set_cpml_local(vel, R=1e-5)
     assert status(lambda: sim.set_staggered(True)) == _lib.EUNSUPPORTED
     sim.step(2)
-    assert status(lambda: sim.adjoint(2)) == _lib.EUNSUPPORTED
+    gprof = torch.zeros((3, 3, 16), device="cuda")
+    assert status(lambda: sim.adjoint(2, None, None, gprof)) == _lib.EUNSUPPORTED   # per axis and node index
+    sim.adjoint(2)          # the transpose with per-node coefficients is provided
+    sim.sync()
     st = Fdtd(shape, h, 0.4 * h / c, cpml_cells=3, nt_max=4, cpml_local=True)
     st.set_staggered(True)
     st.set_model(vel)
@@ -238,3 +241,58 @@ def test_local_grading_restrictions():
     f16 = Fdtd(shape, h, 0.4 * h / c, cpml_cells=3, nt_max=4, cpml_local=True, storage="f16")
     f16.set_model(vel)
     assert status(lambda: f16.set_cpml_local(vel)) == _lib.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("shape,cells,zchunk,with_rho", [((37, 70, 75), (5, 6, 4, 7, 3, 5), 8, False),
+                                                         ((60, 100, 100), (4, 4, 5, 3, 4, 4), 16, False),
+                                                         ((37, 70, 75), (5, 6, 4, 7, 3, 5), 8, True)])
+def test_local_grading_adjoint_state_and_gradient_match_oracle(monkeypatch, shape, cells, zchunk, with_rho):
+    """The fused adjoint with the per-node (b, a) of the local grading (and a
+    density in one case) after 5 steps against the oracle's transpose, field
+    by field, and dJ/dc at fixed coefficients, on multi-tile grids with
+    ragged tails and two shots (interior CTAs on the 100 x 100 plane)."""
+    monkeypatch.setenv("FDTD_ZCHUNK", str(zchunk))
+    Fdtd = _Fdtd()
+    h = 10.0
+    n, C, nshots = 5, 3, 2
+    vel = synth.layered_model(shape, seed=13, vmin=1500.0, vmax=4500.0, amp_cells=2.0)
+    dt = 0.5 * h / float(vel.max())
+    rho = ((vel / 1500.0) ** 0.25).astype(np.float32) if with_rho else None
+    vt = torch.from_numpy(vel).cuda()
+    sim = Fdtd(shape, h, dt, nshots=nshots, cpml_cells=cells, nt_max=n, checkpoint_every=C, cpml_local=True)
+    sim.set_model(vt, torch.from_numpy(rho).cuda() if with_rho else None)
+    sim.set_cpml_local(vt, R=1e-4)
+    g = _grid(vel, h, dt, cells, 1e-4, rho)
+    refs = []
+    for s in range(nshots):
+        x = synth.random_state(shape, cells, seed=90 + s, **state_scales(h, dt))
+        y = synth.random_state(shape, cells, seed=95 + s)
+        for k in FIELDS:
+            sim.set(k, torch.from_numpy(x[k]).cuda(), s)
+            sim.set("adj_" + k, torch.from_numpy(y[k]).cuda(), s)
+        fwd = O.State(shape)
+        for k in FIELDS:
+            fwd[k] = x[k].astype(np.float64)
+        starts = []
+        for _ in range(n):
+            starts.append(fwd.copy())
+            O.run(g, fwd, 1)
+        adj = O.State(shape)
+        for k in FIELDS:
+            adj[k] = y[k].astype(np.float64)
+        gK = np.zeros(shape)
+        for k in range(n - 1, -1, -1):
+            O.adjoint_step(g, starts[k], adj, gK)
+        refs.append((adj, gK))
+    sim.step(n)
+    grad = torch.zeros(shape, device="cuda")
+    sim.adjoint(n, None, grad)
+    sim.sync()
+    for s in range(nshots):
+        for k in FIELDS:
+            e2, em = rel_errors(sim.get("adj_" + k, s).cpu().numpy(), refs[s][0][k])
+            assert e2 <= 1e-4 and em <= 1e-3, (s, k, e2, em)
+    r = rho.astype(np.float64) if with_rho else 1.0
+    gref = (refs[0][1] + refs[1][1]) * 2.0 * r * vel.astype(np.float64)
+    e2, em = rel_errors(grad.cpu().numpy(), gref)
+    assert e2 <= 1e-4 and em <= 1e-3, (e2, em)
