@@ -232,6 +232,39 @@ void og_run(const og_grid *g, og_state *st, long n0, long nsteps,
  * -a_l/h * y_i to i - l e_d (targets outside the grid receive nothing, since
  * the gather never reads there; periodic mode wraps).  Serial on purpose.
  */
+/*
+ * Transposes of the staggered derivatives, as scatters of the gathers in
+ * og_deriv_fwd / og_deriv_bwd: node i sends +c_l/h y_i to i + l (fwd) or
+ * i + l - 1 (bwd) and -c_l/h y_i to i + 1 - l (fwd) or i - l (bwd); targets
+ * outside the grid receive nothing (periodic mode wraps).
+ */
+static void og_stag_transpose_acc(const og_grid *g, const double *y, int axis, int fwd, double *out)
+{
+    long nx = g->nx, ny = g->ny, nz = g->nz;
+    long dz = axis == 2, dy = axis == 1, dx = axis == 0;
+    for (long z = 0; z < nz; z++)
+        for (long yy = 0; yy < ny; yy++)
+            for (long x = 0; x < nx; x++) {
+                double val = y[(z * ny + yy) * nx + x] / g->h;
+                if (val == 0.0)
+                    continue;
+                for (int l = 1; l <= 4; l++) {
+                    const long offs[2] = {fwd ? l : l - 1, fwd ? 1 - l : -l};
+                    for (int s = 0; s < 2; s++) {
+                        long tz = z + offs[s] * dz, ty = yy + offs[s] * dy, tx = x + offs[s] * dx;
+                        if (g->periodic) {
+                            tx = ((tx % nx) + nx) % nx;
+                            ty = ((ty % ny) + ny) % ny;
+                            tz = ((tz % nz) + nz) % nz;
+                        } else if (tx < 0 || tx >= nx || ty < 0 || ty >= ny || tz < 0 || tz >= nz) {
+                            continue;
+                        }
+                        out[(tz * ny + ty) * nx + tx] += (s == 0 ? 1.0 : -1.0) * g->w[l - 1] * val;
+                    }
+                }
+            }
+}
+
 static void og_deriv_transpose_acc(const og_grid *g, const double *y, int axis, double *out)
 {
     long nx = g->nx, ny = g->ny, nz = g->nz;
@@ -277,9 +310,11 @@ static void og_deriv_transpose_acc(const og_grid *g, const double *y, int axis, 
  * (CPML terms only inside the d-slab; kr_d = 1 unless anisotropic), is
  * transposed assignment by assignment in reverse order.  The source term is a
  * constant and has no adjoint.
- * Collocated form (g->staggered = 0); with the local grading (bn, an) the
- * per-node coefficients are transposed the same way, and gprof, which is
- * per axis and node index, is for the 1D profiles only.
+ * The staggered form transposes its own operators (D+ for p -> v, D- for
+ * v -> p) and the half-node velocity profiles; with the local grading (bn,
+ * an) the per-node coefficients are transposed the same way.  gprof, per
+ * axis and node index of the node profiles, is for the collocated form with
+ * 1D profiles only.
  */
 void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
                      double *gradK, double *gprof, long nmax)
@@ -312,13 +347,15 @@ void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
         for (long y = 0; y < ny; y++)
             for (long x = 0; x < nx; x++)
                 for (int d = 0; d < 3; d++)
-                    g_d[d][(z * ny + y) * nx + x] = og_deriv(g, f.p, d, z, y, x);
+                    g_d[d][(z * ny + y) * nx + x] = g->staggered ? og_deriv_fwd(g, f.p, d, z, y, x)
+                                                                 : og_deriv(g, f.p, d, z, y, x);
     og_velocity_stage(g, &f);          /* f.v = v^{n+1/2}, f.psiv = psiv after */
     for (long z = 0; z < nz; z++)
         for (long y = 0; y < ny; y++)
             for (long x = 0; x < nx; x++)
                 for (int d = 0; d < 3; d++)
-                    h_d[d][(z * ny + y) * nx + x] = og_deriv(g, f.v[d], d, z, y, x);
+                    h_d[d][(z * ny + y) * nx + x] = g->staggered ? og_deriv_bwd(g, f.v[d], d, z, y, x)
+                                                                 : og_deriv(g, f.v[d], d, z, y, x);
     og_pressure_stage(g, &f, s_all);   /* s_all = bracket of the pressure update */
 
     /* --- p' = p - dt K sum_d (kinv h_d + psip_d') ;  psip_d' = b psip_d + a h_d --- */
@@ -353,9 +390,13 @@ void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
                 }
                 /* identity part of p' = p - ...: adj->p keeps its value */
             }
-    /* h_d = D_d v_d'  =>  lam(v_d') += D_d^T lam_h_d */
-    for (int d = 0; d < 3; d++)
-        og_deriv_transpose_acc(g, lam_h[d], d, adj->v[d]);
+    /* h_d = D_d v_d'  =>  lam(v_d') += D_d^T lam_h_d  (D- in the staggered form) */
+    for (int d = 0; d < 3; d++) {
+        if (g->staggered)
+            og_stag_transpose_acc(g, lam_h[d], d, 0, adj->v[d]);
+        else
+            og_deriv_transpose_acc(g, lam_h[d], d, adj->v[d]);
+    }
 
     /* --- v_d' = v_d - dt/rho (kinv g_d + psiv_d') ; psiv_d' = b psiv_d + a g_d --- */
     for (long z = 0; z < nz; z++)
@@ -366,23 +407,31 @@ void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
                     long k = og_axis_index(d, z, y, x);
                     double r = -g->dt / og_rho(g, i) * adj->v[d][i];
                     if (g->slab[d][k]) {
+                        /* velocity coefficients: half-node profiles in the staggered form */
+                        const double bvk = g->staggered ? g->bv[d][k] : og_b(g, d, i, k);
+                        const double avk = g->staggered ? g->av[d][k] : og_a(g, d, i, k);
+                        const double kvk = g->staggered ? g->kinvv[d][k] : g->kinv[d][k];
                         double lpsi = adj->psiv[d][i] + r;
-                        lam_g[d][i] = g->kinv[d][k] * r + og_a(g, d, i, k) * lpsi;
+                        lam_g[d][i] = kvk * r + avk * lpsi;
                         if (gprof) {
                             gprof[(d * 3 + 0) * nmax + k] += lpsi * fwd->psiv[d][i];
                             gprof[(d * 3 + 1) * nmax + k] += lpsi * g_d[d][i];
                             gprof[(d * 3 + 2) * nmax + k] += r * g_d[d][i];
                         }
-                        adj->psiv[d][i] = og_b(g, d, i, k) * lpsi;
+                        adj->psiv[d][i] = bvk * lpsi;
                     } else {
                         lam_g[d][i] = r;
                     }
                     /* identity part of v_d' = v_d - ...: adj->v keeps its value */
                 }
             }
-    /* g_d = D_d p  =>  lam(p) += sum_d D_d^T lam_g_d */
-    for (int d = 0; d < 3; d++)
-        og_deriv_transpose_acc(g, lam_g[d], d, adj->p);
+    /* g_d = D_d p  =>  lam(p) += sum_d D_d^T lam_g_d  (D+ in the staggered form) */
+    for (int d = 0; d < 3; d++) {
+        if (g->staggered)
+            og_stag_transpose_acc(g, lam_g[d], d, 1, adj->p);
+        else
+            og_deriv_transpose_acc(g, lam_g[d], d, adj->p);
+    }
 
     for (int d = 0; d < 3; d++) {
         free(lam_h[d]);

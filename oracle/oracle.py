@@ -428,10 +428,11 @@ def adjoint_step(grid: Grid, fwd: State, adj: State, gradK=None, gprof=None):
     the end of the step (receiver residuals already added), replaced by the
     adjoint at the start.  gradK: [nz,ny,nx] accumulator of dJ/dK.
     gprof: [3, 3, nmax] accumulator of dJ/d(b, a, kinv) per axis and node
-    (1D profiles only).  The collocated form only (the staggered form has no
-    transpose here); the local grading's per-node (b, a) are transposed too."""
-    assert not grid.staggered, "adjoint_step: collocated form"
-    assert gprof is None or grid.local is None, "adjoint_step: gprof is per axis and node index"
+    (collocated form with 1D profiles only).  The staggered form transposes
+    its own operators and half-node velocity profiles; the local grading's
+    per-node (b, a) are transposed too."""
+    assert gprof is None or (grid.local is None and not grid.staggered), \
+        "adjoint_step: gprof is per axis and node index of the node profiles"
     nmax = max(grid.shape)
     fc = fwd._c()
     ac = adj._c()

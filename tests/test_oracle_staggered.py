@@ -202,3 +202,68 @@ def test_staggered_cpml_absorbs_a_point_source():
         e = np.array(e)
         ratios.append(e[-1] / e.max())
     assert ratios[0] < 1e-4 and ratios[1] > 0.05 and ratios[1] / ratios[0] > 1e3, ratios
+
+
+def _stag_dot(adj_grid_kwargs=None):
+    rng = np.random.default_rng(31)
+    shape, L, h = (10, 11, 12), (2, 3, 3, 2, 2, 3), 10.0
+    rho = rng.uniform(0.8, 2.2, size=shape)
+    c = rng.uniform(1500.0, 2500.0, size=shape)
+    kr = (1.3, 0.8, 1.0)
+    dt = 0.35 * h / (c.max() * np.sqrt(max(kr)))
+    prof = O.make_profiles(shape, L, h, dt, c.max() * np.sqrt(max(kr)), R=1e-5)
+    g = O.Grid(rho * c * c, h, dt, prof, rho=rho, kr=kr, staggered=True)
+    ga = g if adj_grid_kwargs is None else O.Grid(rho * c * c, h, dt, prof, rho=rho, kr=kr, **adj_grid_kwargs)
+    xs = synth.random_state(shape, L, seed=32, v_scale=dt / h, psiv_scale=1 / h, psip_scale=dt / h ** 2,
+                            dtype=np.float64)
+    ys = synth.random_state(shape, L, seed=33, dtype=np.float64)
+    x, y = O.State(shape), O.State(shape)
+    for k in O.FIELDS:
+        x[k] = xs[k]
+        y[k] = ys[k]
+    fx = x.copy()
+    O.run(g, fx, 6)
+    aty = y.copy()
+    for _ in range(6):
+        O.adjoint_step(ga, O.State(shape), aty)
+    return float(np.dot(fx.as_vector(), y.as_vector())), float(np.dot(x.as_vector(), aty.as_vector()))
+
+
+def test_staggered_transpose_dot_product():
+    """<F x, y> = <x, F^T y> over 6 staggered steps with unequal CPML layers
+    (half-node velocity profiles), a density and anisotropy."""
+    lhs, rhs = _stag_dot()
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_staggered_dot_product_detects_the_collocated_transpose():
+    lhs, rhs = _stag_dot(dict(weights=O.STAGGERED_WEIGHTS))   # centred operators, staggered weights
+    assert abs(lhs - rhs) > 1e-3 * abs(lhs)
+
+
+def test_staggered_gradient_matches_central_differences():
+    shape, L, h = (14, 13, 15), (3, 3, 2, 3, 3, 2), 10.0
+    rng = np.random.default_rng(12)
+    c_true = rng.uniform(1800, 2600, size=shape)
+    c0 = np.full(shape, 2200.0)
+    dt = 0.4 * h / 2600.0
+    prof = O.make_profiles(shape, L, h, dt, 2600.0, R=1e-5)
+    nt = 50
+    src = (7, 6, 7)
+    wav = synth.ricker(nt, dt, 40.0)
+    rec = np.array([[4, 4, 5], [5, 9, 9], [10, 6, 4], [3, 10, 11], [11, 9, 10]])
+    dobs = O.forward_traces(O.Grid(c_true ** 2, h, dt, prof, staggered=True), nt, src, wav, rec)
+    K0 = c0 ** 2
+    _, gK, _, _ = O.misfit_gradient(O.Grid(K0, h, dt, prof, staggered=True), nt, src, wav, rec, dobs,
+                                    checkpoint_every=9)
+    nodes = [tuple(int(rng.integers(0, s)) for s in shape) for _ in range(5)] + [(7, 6, 8), (0, 0, 0), (13, 12, 14)]
+    scale = np.max(np.abs(gK))
+    for node in nodes:
+        eps = 1e-4 * K0[node]
+        Kp, Km = K0.copy(), K0.copy()
+        Kp[node] += eps
+        Km[node] -= eps
+        Jp, _ = O.misfit(O.Grid(Kp, h, dt, prof, staggered=True), nt, src, wav, rec, dobs)
+        Jm, _ = O.misfit(O.Grid(Km, h, dt, prof, staggered=True), nt, src, wav, rec, dobs)
+        fd = (Jp - Jm) / (2 * eps)
+        assert abs(gK[node] - fd) <= 1e-6 * scale + 1e-5 * abs(fd), (node, gK[node], fd)
