@@ -191,9 +191,11 @@ int fdtd_set_anisotropy(fdtd_ctx *ctx, const double kr[3]);
  * 2 / (sqrt(sum_d kr_d) 2 sum_l |c_l|) = 0.44884 for kr = 1.
  * on = 0 restores the collocated default.  Chosen before the first step
  * (ESTATE after it until fdtd_reset).  EUNSUPPORTED for 16-bit storage, with
- * a density or with learned profiles (fdtd_set_cpml_ska), and the adjoint
- * is not provided (fdtd_adjoint_step_n: EUNSUPPORTED).  EUNSTABLE (form
- * unchanged) if a set model violates the limit; fdtd_set_model checks it. */
+ * a density, with learned profiles (fdtd_set_cpml_ska) or with the local
+ * grading.  fdtd_adjoint_step_n transposes the staggered step (D+^T = -D-,
+ * D-^T = -D+, half-node velocity profiles); the CPML-profile gradient is not
+ * provided for it (grad_cpml: EUNSUPPORTED).  EUNSTABLE (form unchanged) if
+ * a set model violates the limit; fdtd_set_model checks it. */
 int fdtd_set_staggered(fdtd_ctx *ctx, int on);
 
 /* Per-cell (sigma, kappa, alpha) for a layer of L equal cells on every face
@@ -243,9 +245,9 @@ int fdtd_step_n(fdtd_ctx *ctx, int n);
  * [b, a, 1/kappa][node]) receives += dJ/d(profile) and needs cpml_grad at
  * create time (EINVAL otherwise).  Needs FP32 storage,
  * checkpoint_every > 0 and n equal to the current time index (ESTATE
- * otherwise), and the collocated form (EUNSUPPORTED for the staggered form,
- * and for grad_cpml with fdtd_set_cpml_local).  Leaves the forward state
- * undefined (call fdtd_reset). */
+ * otherwise).  grad_cpml is for the collocated form with the 1D grading
+ * (EUNSUPPORTED with the staggered form or fdtd_set_cpml_local).  Leaves the
+ * forward state undefined (call fdtd_reset). */
 int fdtd_adjoint_step_n(fdtd_ctx *ctx, int n, const float *resid_dev,
                         float *grad_vel_dev, float *grad_cpml_dev);
 

@@ -52,7 +52,9 @@ struct FusedLayout {
     static constexpr int GX = W, GY = W + TY * GW;
     static constexpr int CX = W + 2 * TY * AW;     // b, a, 1/kappa over x0-8 .. x0+40
     static constexpr int CY = CX + 3 * AW;         // same over y
-    static constexpr int END = CY + 3 * AW;
+    static constexpr int CXV = CY + 3 * AW;        // the velocity profiles (half nodes when staggered)
+    static constexpr int CYV = CXV + 3 * AW;
+    static constexpr int END = CYV + 3 * AW;
     static constexpr int BYTES = END * 4 + 8 * ANS;
     static_assert((PQ * 4) % 128 == 0 && (VX * 4) % 128 == 0 && (VY * 4) % 128 == 0 && (VZ * 4) % 128 == 0 &&
                       (KT * 4) % 128 == 0 && (STAGE * 4) % 128 == 0,
@@ -74,6 +76,7 @@ struct FusedArgs {
     const float *apsip_in[3];
     float *apsip_out[3];
     const float *cb[3], *ca[3], *ck[3];
+    const float *cbv[3], *cav[3], *ckv[3];   // velocity profiles (half nodes when staggered, else cb..)
     float c[4];
     float dtr;
     float dt_over_vs;
@@ -119,6 +122,14 @@ __device__ __forceinline__ F4 f4z() { return F4{{0.f, 0.f, 0.f, 0.f}}; }
 __device__ __forceinline__ float2 ld2s(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 
 // D along a row: outputs at columns c0 .. c0+3 of `row` (c0 - 4 >= 0, c0 % 4 == 0)
+// Stencil modes: 0 centred (offsets +l, -l); 1 staggered forward, node ->
+// half node (+l, 1-l); 2 staggered backward, half node -> node (l-1, -l).
+template <int M>
+__host__ __device__ constexpr int offp(int l) { return M == 2 ? l - 1 : l; }
+template <int M>
+__host__ __device__ constexpr int offm(int l) { return M == 1 ? 1 - l : -l; }
+
+template <int M>
 __device__ __forceinline__ F4 drow(const float *row, int c0, const float *w)
 {
     const F4 a = ld4s(row + c0 - 4), b = ld4s(row + c0), c = ld4s(row + c0 + 4);
@@ -126,12 +137,15 @@ __device__ __forceinline__ F4 drow(const float *row, int c0, const float *w)
     F4 r;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-        r.v[i] = w[0] * (f[i + 5] - f[i + 3]) + w[1] * (f[i + 6] - f[i + 2]) + w[2] * (f[i + 7] - f[i + 1]) +
-                 w[3] * (f[i + 8] - f[i]);
+        r.v[i] = w[0] * (f[i + 4 + offp<M>(1)] - f[i + 4 + offm<M>(1)]) +
+                 w[1] * (f[i + 4 + offp<M>(2)] - f[i + 4 + offm<M>(2)]) +
+                 w[2] * (f[i + 4 + offp<M>(3)] - f[i + 4 + offm<M>(3)]) +
+                 w[3] * (f[i + 4 + offp<M>(4)] - f[i + 4 + offm<M>(4)]);
     return r;
 }
 
 // the same for one pair of outputs at columns c0, c0+1 (c0 even, c0 - 4 >= 0)
+template <int M>
 __device__ __forceinline__ float2 drow2(const float *row, int c0, const float *w)
 {
     float f[10];
@@ -141,19 +155,24 @@ __device__ __forceinline__ float2 drow2(const float *row, int c0, const float *w
         f[2 * k] = v.x;
         f[2 * k + 1] = v.y;
     }
-    float2 r;
-    r.x = w[0] * (f[5] - f[3]) + w[1] * (f[6] - f[2]) + w[2] * (f[7] - f[1]) + w[3] * (f[8] - f[0]);
-    r.y = w[0] * (f[6] - f[4]) + w[1] * (f[7] - f[3]) + w[2] * (f[8] - f[2]) + w[3] * (f[9] - f[1]);
-    return r;
+    float o[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        o[i] = w[0] * (f[i + 4 + offp<M>(1)] - f[i + 4 + offm<M>(1)]) +
+               w[1] * (f[i + 4 + offp<M>(2)] - f[i + 4 + offm<M>(2)]) +
+               w[2] * (f[i + 4 + offp<M>(3)] - f[i + 4 + offm<M>(3)]) +
+               w[3] * (f[i + 4 + offp<M>(4)] - f[i + 4 + offm<M>(4)]);
+    return make_float2(o[0], o[1]);
 }
 
-// D along a column of a plane with `stride`: rows r0 -+ l, 4 columns at c
+// D along a column of a plane with `stride`: rows r0 + offp, r0 + offm, 4 columns at c
+template <int M>
 __device__ __forceinline__ F4 dcol(const float *plane, int stride, int r0, int c, const float *w)
 {
     F4 r = f4z();
 #pragma unroll
     for (int l = 1; l <= 4; ++l) {
-        const F4 p = ld4s(plane + (r0 + l) * stride + c), m = ld4s(plane + (r0 - l) * stride + c);
+        const F4 p = ld4s(plane + (r0 + offp<M>(l)) * stride + c), m = ld4s(plane + (r0 + offm<M>(l)) * stride + c);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             r.v[i] += w[l - 1] * (p.v[i] - m.v[i]);
@@ -161,12 +180,13 @@ __device__ __forceinline__ F4 dcol(const float *plane, int stride, int r0, int c
     return r;
 }
 
+template <int M>
 __device__ __forceinline__ float2 dcol2(const float *plane, int stride, int r0, int c, const float *w)
 {
     float2 r = make_float2(0.f, 0.f);
 #pragma unroll
     for (int l = 1; l <= 4; ++l) {
-        const float2 p = ld2s(plane + (r0 + l) * stride + c), m = ld2s(plane + (r0 - l) * stride + c);
+        const float2 p = ld2s(plane + (r0 + offp<M>(l)) * stride + c), m = ld2s(plane + (r0 + offm<M>(l)) * stride + c);
         r.x += w[l - 1] * (p.x - m.x);
         r.y += w[l - 1] * (p.y - m.y);
     }
@@ -174,13 +194,16 @@ __device__ __forceinline__ float2 dcol2(const float *plane, int stride, int r0, 
 }
 
 // D_z at the centre of a 9-plane queue
+template <int M>
 __device__ __forceinline__ F4 dq(const F4 *q, const float *w)
 {
     F4 r;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-        r.v[i] = w[0] * (q[5].v[i] - q[3].v[i]) + w[1] * (q[6].v[i] - q[2].v[i]) + w[2] * (q[7].v[i] - q[1].v[i]) +
-                 w[3] * (q[8].v[i] - q[0].v[i]);
+        r.v[i] = w[0] * (q[4 + offp<M>(1)].v[i] - q[4 + offm<M>(1)].v[i]) +
+                 w[1] * (q[4 + offp<M>(2)].v[i] - q[4 + offm<M>(2)].v[i]) +
+                 w[2] * (q[4 + offp<M>(3)].v[i] - q[4 + offm<M>(3)].v[i]) +
+                 w[3] * (q[4 + offp<M>(4)].v[i] - q[4 + offm<M>(4)].v[i]);
     return r;
 }
 
@@ -215,15 +238,19 @@ __device__ __forceinline__ void st_own(float *p, const F4 &v, int nv)
 // staged mu plane directly.  kEdge = true forms lam_h in shared memory first.
 // kRho: the velocity transpose takes -dtr / rho per node from A.nbr.
 // kLocal: b and a of every slab node come from A.lb, A.la (local grading).
-template <bool kEdge, bool kRho, bool kLocal>
+// kStag: the staggered form's transpose: stage A applies D+ to lam_h, stage B
+// D- to lam_g, and the velocity transpose takes the half-node profiles.
+template <bool kEdge, bool kRho, bool kLocal, bool kStag>
 __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMap &mPq, const CUtensorMap &mVX,
                                          const CUtensorMap &mVY, const CUtensorMap &mVZ, const CUtensorMap &mK,
                                          const FusedArgs &A, int z0, int z1, float *sm)
 {
     using L = FusedLayout;
+    constexpr int kSA = kStag ? 1 : 0, kSB = kStag ? 2 : 0;   // stencil modes of stages A and B
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::END);
     float *HX = sm + L::HX, *HY = sm + L::HY, *GX = sm + L::GX, *GY = sm + L::GY;
     float *sCx = sm + L::CX, *sCy = sm + L::CY;   // [3][48]: b, a, 1/kappa
+    float *sCxv = kStag ? sm + L::CXV : sCx, *sCyv = kStag ? sm + L::CYV : sCy;   // velocity transpose
     const Geom &G = A.g;
     const int tid = threadIdx.x, tx = tid % (TX / 4), ty = tid / (TX / 4);
     const int tile = blockIdx.x;
@@ -257,6 +284,10 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
         const bool iny = y >= 0 && y < G.ny && in_slab(y, G.ny, G.lo[1], G.hi[1]);
         sCx[i] = inx ? (c == 0 ? A.cb[0][x] : (c == 1 ? A.ca[0][x] : A.ck[0][x])) : (c == 2 ? 1.f : 0.f);
         sCy[i] = iny ? (c == 0 ? A.cb[1][y] : (c == 1 ? A.ca[1][y] : A.ck[1][y])) : (c == 2 ? 1.f : 0.f);
+        if (kStag) {
+            sCxv[i] = inx ? (c == 0 ? A.cbv[0][x] : (c == 1 ? A.cav[0][x] : A.ckv[0][x])) : (c == 2 ? 1.f : 0.f);
+            sCyv[i] = iny ? (c == 0 ? A.cbv[1][y] : (c == 1 ? A.cav[1][y] : A.ckv[1][y])) : (c == 2 ? 1.f : 0.f);
+        }
     }
 
     // halo task: one pair of nodes.  Threads 0..127: lam_v'_y on the y halo
@@ -413,7 +444,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
             const int zv = t + 4;
             F4 gn = f4z();
             if (ok && zv >= 0 && zv < G.nz) {
-                const F4 dh = dq(hq, w);
+                const F4 dh = dq<kSA>(hq, w);
                 F4 vz = ld4s(S + L::VZ + ty * TX + 4 * tx);
                 F4 fz = F4{{ndtr, ndtr, ndtr, ndtr}};
                 if (kRho)
@@ -430,15 +461,15 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                     const long long si = slab_index(G, 2, zv, gy, gx);
                     const F4 ps = ld4s(psvin[2] + si);
                     if (owned) {
-                        const F4 b = kLocal ? ldc4(A.lb[2] + si) : f4s(__ldg(A.cb[2] + zv));
+                        const F4 b = kLocal ? ldc4(A.lb[2] + si) : f4s(__ldg(A.cbv[2] + zv));
                         F4 pn;
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
                             pn.v[i] = b.v[i] * (ps.v[i] + gn.v[i]);
                         st4s(psvout[2] + si, pn);
                     }
-                    const F4 a = kLocal ? ldc4(A.la[2] + si) : f4s(__ldg(A.ca[2] + zv));
-                    const float kk = __ldg(A.ck[2] + zv);
+                    const F4 a = kLocal ? ldc4(A.la[2] + si) : f4s(__ldg(A.cav[2] + zv));
+                    const float kk = __ldg(A.ckv[2] + zv);
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
                         gn.v[i] = corr1(gn.v[i], ps.v[i], a.v[i], kk);
@@ -446,7 +477,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
             }
             gq[8] = gn;
         }
-        const F4 hz = dq(gq, w);
+        const F4 hz = dq<kSB>(gq, w);
 
         // sources of D_x lam_h_x (row r <-> y0 + r, column c <-> x0 - 8 + c)
         // and D_y lam_h_y (row r <-> y0 - 8 + r, column c <-> x0 + c): shared
@@ -527,7 +558,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 fo4 = row_ok ? Io<float>::ldg4(A.nbr + (long long)t * G.plane + rowofs) : f4z();
             {
                 F4 vx = ld4s(S + L::VX + ty * GW + 4 * tx + 4);
-                const F4 dh = drow(hxs + ty * hxw, 4 * tx + AH, w);
+                const F4 dh = drow<kSA>(hxs + ty * hxw, 4 * tx + AH, w);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     vx.v[i] -= kxs * dh.v[i];
@@ -537,15 +568,15 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                     const long long si = slab_index(G, 0, t, gy, gx);
                     const F4 ps = ld4s(psvin[0] + si);
                     const int c0 = 4 * tx + AH;
-                    const F4 b = kLocal ? ldc4(A.lb[0] + si) : F4{{sCx[c0], sCx[c0 + 1], sCx[c0 + 2], sCx[c0 + 3]}};
+                    const F4 b = kLocal ? ldc4(A.lb[0] + si) : F4{{sCxv[c0], sCxv[c0 + 1], sCxv[c0 + 2], sCxv[c0 + 3]}};
                     const F4 a = kLocal ? ldc4(A.la[0] + si)
-                                        : F4{{sCx[AW + c0], sCx[AW + c0 + 1], sCx[AW + c0 + 2], sCx[AW + c0 + 3]}};
+                                        : F4{{sCxv[AW + c0], sCxv[AW + c0 + 1], sCxv[AW + c0 + 2], sCxv[AW + c0 + 3]}};
                     F4 pn;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int cc = c0 + i;
                         pn.v[i] = b.v[i] * (ps.v[i] + gxo.v[i]);
-                        gxo.v[i] = corr1(gxo.v[i], ps.v[i], a.v[i], sCx[2 * AW + cc]);
+                        gxo.v[i] = corr1(gxo.v[i], ps.v[i], a.v[i], sCxv[2 * AW + cc]);
                     }
                     st4s(psvout[0] + si, pn);
                 }
@@ -554,7 +585,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
             }
             {
                 F4 vy = ld4s(S + L::VY + (ty + 4) * TX + 4 * tx);
-                const F4 dh = dcol(hys, hyw, ty + AH, 4 * tx, w);
+                const F4 dh = dcol<kSA>(hys, hyw, ty + AH, 4 * tx, w);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     vy.v[i] -= kys * dh.v[i];
@@ -563,9 +594,9 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                 if (own_y) {
                     const long long si = slab_index(G, 1, t, gy, gx);
                     const F4 ps = ld4s(psvin[1] + si);
-                    const F4 b = kLocal ? ldc4(A.lb[1] + si) : f4s(sCy[ty + AH]);
-                    const F4 a = kLocal ? ldc4(A.la[1] + si) : f4s(sCy[AW + ty + AH]);
-                    const float kk = sCy[2 * AW + ty + AH];
+                    const F4 b = kLocal ? ldc4(A.lb[1] + si) : f4s(sCyv[ty + AH]);
+                    const F4 a = kLocal ? ldc4(A.la[1] + si) : f4s(sCyv[AW + ty + AH]);
+                    const float kk = sCyv[2 * AW + ty + AH];
                     F4 pn;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -588,7 +619,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
             if (do_yhalo) {
                 const int r = yh_y - y0 + 4, c = yh_x - x0;
                 float2 vy = ld2s(S + L::VY + r * TX + c);
-                const float2 dh = dcol2(hys, hyw, yh_y - y0 + AH, c, w);
+                const float2 dh = dcol2<kSA>(hys, hyw, yh_y - y0 + AH, c, w);
                 float2 fh = make_float2(ndtr, ndtr);
                 if (kRho)
                     fh = (yh_in && yh_x < G.nxp)
@@ -600,8 +631,8 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                     if (ys_tile && yh_in && yh_x < G.nxp && in_slab(yh_y, G.ny, G.lo[1], G.hi[1])) {
                         const long long ih = slab_index(G, 1, t, yh_y, yh_x);
                         const float2 ps = ld2s(psvin[1] + ih);
-                        const float2 a = kLocal ? ldc2(A.la[1] + ih) : make_float2(sCy[AW + r + 4], sCy[AW + r + 4]);
-                        const float kk = sCy[2 * AW + r + 4];
+                        const float2 a = kLocal ? ldc2(A.la[1] + ih) : make_float2(sCyv[AW + r + 4], sCyv[AW + r + 4]);
+                        const float kk = sCyv[2 * AW + r + 4];
                         gh.x = corr1(gh.x, ps.x, a.x, kk);
                         gh.y = corr1(gh.y, ps.y, a.y, kk);
                     }
@@ -611,7 +642,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
             } else {
                 const int r = xh_y - y0, c = xh_x - x0 + 4;
                 float2 vx = ld2s(S + L::VX + r * GW + c);
-                const float2 dh = drow2(hxs + r * hxw, xh_x - x0 + AH, w);
+                const float2 dh = drow2<kSA>(hxs + r * hxw, xh_x - x0 + AH, w);
                 float2 fh = make_float2(ndtr, ndtr);
                 if (kRho)
                     fh = (xh_in && xh_x >= 0 && xh_x < G.nxp)
@@ -625,9 +656,9 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
                         const long long ih = slab_index(G, 0, t, xh_y, xh_x);
                         const float2 ps = ld2s(psvin[0] + ih);
                         const int cc = xh_x - x0 + AH;
-                        const float2 a = kLocal ? ldc2(A.la[0] + ih) : make_float2(sCx[AW + cc], sCx[AW + cc + 1]);
-                        gh.x = corr1(gh.x, ps.x, a.x, sCx[2 * AW + cc]);
-                        gh.y = corr1(gh.y, ps.y, a.y, sCx[2 * AW + cc + 1]);
+                        const float2 a = kLocal ? ldc2(A.la[0] + ih) : make_float2(sCxv[AW + cc], sCxv[AW + cc + 1]);
+                        gh.x = corr1(gh.x, ps.x, a.x, sCxv[2 * AW + cc]);
+                        gh.y = corr1(gh.y, ps.y, a.y, sCxv[2 * AW + cc + 1]);
                     }
                     gh.x = (xh_in && xh_x >= 0 && xh_x < G.nx) ? gh.x : 0.f;
                     gh.y = (xh_in && xh_x + 1 >= 0 && xh_x + 1 < G.nx) ? gh.y : 0.f;
@@ -691,8 +722,8 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
         if (active && row_ok) {
             // ---- stage B: mu' = mu - kdt (D_x lam_g_x + D_y lam_g_y + D_z lam_g_z)
             const long long o = fo + (long long)t * G.plane + rowofs;
-            const F4 d1 = drow(GX + ty * GW, 4 * tx + 4, w);
-            const F4 d2 = dcol(GY, TX, ty + 4, 4 * tx, w);
+            const F4 d1 = drow<kSB>(GX + ty * GW, 4 * tx + 4, w);
+            const F4 d2 = dcol<kSB>(GY, TX, ty + 4, 4 * tx, w);
             const F4 kd = ld4s(S + L::KT + ty * TX + 4 * tx);
             F4 mu = ld4s(S + L::P + (ty + AH) * AW + 4 * tx + AH);
 #pragma unroll
@@ -713,7 +744,7 @@ __device__ __forceinline__ void adj_body(const CUtensorMap &mP, const CUtensorMa
     }
 }
 
-template <bool kRho, bool kLocal>
+template <bool kRho, bool kLocal, bool kStag>
 __global__ void __launch_bounds__(NTHREADS, 2)
     adj_fused_kernel(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mPq,
                      const __grid_constant__ CUtensorMap mVX, const __grid_constant__ CUtensorMap mVY,
@@ -729,9 +760,9 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     const bool interior = x0 - AH >= G.lo[0] && x0 + TX + AH <= G.nx - G.hi[0] && y0 - AH >= G.lo[1] &&
                           y0 + TY + AH <= G.ny - G.hi[1] && z0 - 8 >= G.lo[2] && z1 + 8 <= G.nz - G.hi[2];
     if (interior)
-        adj_body<false, kRho, false>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
+        adj_body<false, kRho, false, kStag>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
     else
-        adj_body<true, kRho, kLocal>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
+        adj_body<true, kRho, kLocal, kStag>(mP, mPq, mVX, mVY, mVZ, mK, A, z0, z1, sm);
 }
 
 }  // namespace
@@ -742,10 +773,13 @@ cudaError_t adjoint_step_fused(fdtd_ctx *c, const float *s_tape)
 {
     static bool attr_done = false;
     if (!attr_done) {
-        const void *kern[4] = {(const void *)adj_fused_kernel<false, false>, (const void *)adj_fused_kernel<true, false>,
-                               (const void *)adj_fused_kernel<false, true>, (const void *)adj_fused_kernel<true, true>};
+        const void *kern[5] = {(const void *)adj_fused_kernel<false, false, false>,
+                               (const void *)adj_fused_kernel<true, false, false>,
+                               (const void *)adj_fused_kernel<false, true, false>,
+                               (const void *)adj_fused_kernel<true, true, false>,
+                               (const void *)adj_fused_kernel<false, false, true>};
         cudaError_t e = cudaSuccess;
-        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        for (int k = 0; k < 5 && e == cudaSuccess; ++k)
             e = cudaFuncSetAttribute(kern[k], cudaFuncAttributeMaxDynamicSharedMemorySize, FusedLayout::BYTES);
         if (e != cudaSuccess)
             return e;
@@ -783,9 +817,13 @@ cudaError_t adjoint_step_fused(fdtd_ctx *c, const float *s_tape)
         a.cb[d] = c->coef + (d * 3 + 0) * nmax;
         a.ca[d] = c->coef + (d * 3 + 1) * nmax;
         a.ck[d] = c->coef + (d * 3 + 2) * nmax;
+        const int hv = c->staggered ? 9 : 0;   // half-node tables follow the node tables
+        a.cbv[d] = c->coef + (hv + d * 3 + 0) * nmax;
+        a.cav[d] = c->coef + (hv + d * 3 + 1) * nmax;
+        a.ckv[d] = c->coef + (hv + d * 3 + 2) * nmax;
     }
     for (int l = 0; l < 4; ++l)
-        a.c[l] = (float)(kWeights[l] / c->d.h);
+        a.c[l] = (float)((c->staggered ? kStagWeights[l] : kWeights[l]) / c->d.h);
     a.dtr = (float)(c->d.dt * c->vscale);
     a.dt_over_vs = (float)(c->d.dt / c->vscale);
     for (int d = 0; d < 3; ++d)
@@ -801,17 +839,20 @@ cudaError_t adjoint_step_fused(fdtd_ctx *c, const float *s_tape)
     dim3 grid(c->tiles_x * c->tiles_y, adj_chunks(a), c->d.nshots);
     const CUtensorMap *m = c->amaps[s];
     const bool loc = a.lb[0] != nullptr;
-    if (a.nbr && loc)
-        adj_fused_kernel<true, true><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3], m[4],
+    if (c->staggered)   // constant density and the 1D grading (the API enforces both)
+        adj_fused_kernel<false, false, true><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(
+            m[0], m[1], m[2], m[3], m[4], c->mapK, a);
+    else if (a.nbr && loc)
+        adj_fused_kernel<true, true, false><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3], m[4],
                                                                                         c->mapK, a);
     else if (a.nbr)
-        adj_fused_kernel<true, false><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3],
+        adj_fused_kernel<true, false, false><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3],
                                                                                          m[4], c->mapK, a);
     else if (loc)
-        adj_fused_kernel<false, true><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3],
+        adj_fused_kernel<false, true, false><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3],
                                                                                          m[4], c->mapK, a);
     else
-        adj_fused_kernel<false, false><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3],
+        adj_fused_kernel<false, false, false><<<grid, NTHREADS, FusedLayout::BYTES, c->stream>>>(m[0], m[1], m[2], m[3],
                                                                                           m[4], c->mapK, a);
     const cudaError_t e = cudaGetLastError();
     c->aset ^= 1;

@@ -1145,8 +1145,8 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
         return fail(c, FDTD_ESTATE, "n must equal the current time index (%d) and be <= nt_max", c->t);
     if (grad_cpml && !c->d.cpml_grad)
         return fail(c, FDTD_EINVAL, "grad_cpml needs cpml_grad at create time");
-    if (c->staggered)
-        return fail(c, FDTD_EUNSUPPORTED, "the adjoint is provided for the collocated form only");
+    if (c->staggered && grad_cpml)
+        return fail(c, FDTD_EUNSUPPORTED, "the CPML-profile gradient is for the collocated form (node profiles)");
     if (c->cpml_local_set && grad_cpml)
         return fail(c, FDTD_EUNSUPPORTED, "the CPML-profile gradient is for the 1D grading (per axis and node)");
     const bool want_prof = grad_cpml != nullptr;
