@@ -124,3 +124,9 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.fdtd_step_n(None, 1) == _lib.EINVAL
     assert lib.fdtd_destroy(None) == _lib.EINVAL
     assert lib.fdtd_last_error(None) == b"context is NULL"
+    # the setters of the step's forms check their context before anything else
+    assert lib.fdtd_set_staggered(None, 1) == _lib.EINVAL
+    assert lib.fdtd_set_cpml_local(None, None, 1e-8, 5.0, 0.05, 3) == _lib.EINVAL
+    assert lib.fdtd_set_anisotropy(None, None) == _lib.EINVAL
+    assert lib.fdtd_set_model(None, None, None) == _lib.EINVAL
+    assert lib.fdtd_adjoint_step_n(None, 0, None, None, None) == _lib.EINVAL
