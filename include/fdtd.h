@@ -224,12 +224,13 @@ int fdtd_record(fdtd_ctx *ctx, const int *rec_zyx, int nrec, float *traces_dev);
  *
  * Temporal blocking, tblock_k = k in {2, 4} (the enlarged-ghost idea of
  * paper Sec. 3.3, g = 2 r s, applied to z bands of one device): whole
- * blocks of k steps cut the z range into bands of >= 8 planes (48 by
- * default, environment variable FDTD_TBAND); step s of a block runs on a
- * band as soon as step s - 1 has finished that band and its two neighbours,
- * so a band's intermediate states are read back while they can still be held
- * in L2.  The library then enqueues on k internal streams that join `stream`
- * before the call returns (events; no host wait).  Results are identical to
+ * blocks of k steps cut the z range into bands of >= 8 planes (96 by
+ * default, environment variable FDTD_TBAND), each launched in chunks of at
+ * most 32 planes (96 with 16-bit storage; FDTD_TBCHUNK); step s of a block
+ * runs on a band as soon as step s - 1 has finished that band and its two
+ * neighbours, so the k steps' launches overlap.  The library enqueues on k
+ * internal streams that join `stream` before the call returns (events; no
+ * host wait).  Results are identical to
  * k = 1, node for node.  Steps left over after the whole blocks, and any
  * block with a checkpoint inside it, run as single steps. */
 int fdtd_step_n(fdtd_ctx *ctx, int n);
