@@ -607,12 +607,18 @@ def oracle_sample(preset: str, nsteps: int, warm: int = 0):
     return float(np.prod(w.shape)) * nsteps / dt / 1e6, dt, threads
 
 
+def state_gb(shape, storage):
+    """Device bytes of the stepped state: p and v in two sets plus the FP32 K table."""
+    es = 4 if storage == "f32" else 2
+    return (8 * es + 4) * float(np.prod(shape)) / 1e9
+
+
 def workload_config(args, shape, cells, nt, world):
     out = {"workload": f"{args.preset}: {shape[0]}^3 layered 1500-4500 m/s, CPML {cells[0]} cells, "
                        f"R=1e-8, 10 Hz Ricker, {nt} time steps per bench step",
            "grid": list(shape), "time_steps_per_step": nt, "cpml_cells": list(cells),
            "storage": args.storage, "parallelism": f"replicas x{world}",
-           "l2": "inputs larger than L2 (state >= 4 GB per replica)"}
+           "l2": f"inputs larger than L2 (state {state_gb(shape, args.storage):.1f} GB per replica, L2 129 MB)"}
     if getattr(args, "variant", "plain") != "plain":
         out["variant"] = args.variant
     return out
