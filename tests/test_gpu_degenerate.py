@@ -1,8 +1,9 @@
 """Degenerate grids through the C ABI against the FP64 oracle: lines along z
 and x, a single z plane, axes whose every node lies in the CPML, z extents
 below the stencil's reach, one tile with most of its nodes beyond the grid,
-and the 16-bit and blocked paths on such grids.  Random states (memory
-variables only inside their slabs) and a 1D source run."""
+and the 16-bit, blocked, staggered, local-grading and adjoint paths on such
+grids.  Random states (memory variables only inside their slabs) and a 1D
+source run."""
 import numpy as np
 import pytest
 
@@ -122,3 +123,61 @@ def test_degenerate_grid_blocked_equals_single_steps(shape, cells):
         out.append({f: sim.get(f) for f in FIELDS})
     for f in FIELDS:
         assert torch.equal(out[0][f], out[1][f]), f
+
+
+@pytest.mark.parametrize("shape,cells", CASES)
+def test_degenerate_grid_staggered_and_local(shape, cells):
+    """The staggered form and the local CPML grading on the same grids,
+    random state, 7 steps, against the oracle's forms."""
+    Fdtd = _Fdtd()
+    h, c = 10.0, 2500.0
+    rng = np.random.default_rng(23)
+    vel = rng.uniform(1500.0, c, size=shape).astype(np.float32)
+    vt = torch.from_numpy(vel).cuda()
+    for form in ("staggered", "local"):
+        dt = (0.4 if form == "staggered" else 0.5) * h / c
+        state = synth.random_state(shape, cells, seed=24, **state_scales(h, dt))
+        sim = Fdtd(shape, h, dt, cpml_cells=cells, nt_max=8, cpml_local=form == "local")
+        if form == "staggered":
+            sim.set_staggered(True)
+        sim.set_model(vt)
+        if form == "local":
+            sim.set_cpml_local(vt, R=1e-5)
+        else:
+            sim.set_cpml(R=1e-5, c_ref=c)
+        set_gpu_state(sim, state)
+        sim.step(7)
+        sim.sync()
+        v = vel.astype(np.float64)
+        prof = O.make_profiles(shape, cells, h, dt, c if form == "staggered" else float(v.max()), R=1e-5)
+        g = O.Grid(v * v, h, dt, prof, staggered=form == "staggered",
+                   local=O.local_profiles(v, cells, h, dt, R=1e-5) if form == "local" else None)
+        st = oracle_state(shape, state)
+        O.run(g, st, 7)
+        _check_all(gpu_fields(sim), st)
+
+
+@pytest.mark.parametrize("shape,cells", [CASES[0], CASES[2], CASES[3], CASES[4]])
+def test_degenerate_grid_adjoint_dot_product(shape, cells):
+    """<F x, y> = <x, F^T y> through the library's adjoint on the degenerate
+    grids (6 steps, checkpoints every 3)."""
+    Fdtd = _Fdtd()
+    h, c = 10.0, 2500.0
+    dt = 0.5 * h / c
+    rng = np.random.default_rng(25)
+    vel = rng.uniform(1500.0, c, size=shape).astype(np.float32)
+    sim = Fdtd(shape, h, dt, cpml_cells=cells, nt_max=8, checkpoint_every=3)
+    sim.set_model(torch.from_numpy(vel).cuda())
+    sim.set_cpml(R=1e-4, c_ref=c)
+    x = synth.random_state(shape, cells, seed=26, **state_scales(h, dt))
+    y = synth.random_state(shape, cells, seed=27)
+    for k in FIELDS:
+        sim.set(k, torch.from_numpy(x[k]).cuda())
+        sim.set("adj_" + k, torch.from_numpy(y[k]).cuda())
+    sim.step(6)
+    fx = {k: sim.get(k).cpu().numpy().astype(np.float64) for k in FIELDS}
+    sim.adjoint(6)
+    aty = {k: sim.get("adj_" + k).cpu().numpy().astype(np.float64) for k in FIELDS}
+    lhs = sum(float(np.sum(fx[k] * y[k])) for k in FIELDS)
+    rhs = sum(float(np.sum(x[k].astype(np.float64) * aty[k])) for k in FIELDS)
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs)), (lhs, rhs)
