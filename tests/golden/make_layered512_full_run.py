@@ -1,12 +1,14 @@
-"""Writes tests/golden/layered512_full_run.txt: the FP64 oracle's result of
-the full 512^3 layered workload (Sec. 3.1-3.2 step; 20-cell CPML with
-R = 1e-8, 10 Hz Ricker source 30 cells below the top face, c_max dt / h = 0.5,
-1000 steps), at 72 fixed receivers every 10th step and at 128 sampled nodes
-of p after the last step.  It calls only the oracle and the seeded input
-generators; the GPU parity test reads the file.  Runs in about two hours on
-8 CPU threads and needs about 13 GB of memory.
+"""Writes tests/golden/layered512_full_run[_<form>].txt: the FP64 oracle's
+result of the full 512^3 layered workload (Sec. 3.1-3.2 step; 20-cell CPML
+with R = 1e-8, 10 Hz Ricker source 30 cells below the top face, 1000 steps),
+at 72 fixed receivers every 10th step and at 128 sampled nodes of p after the
+last step.  Forms: plain (c_max dt / h = 0.5), staggered (the Yee form at
+0.4), density (rho = (c / 1500)^(1/4) per node), local (the CPML graded from
+the velocity at each slab node).  It calls only the oracle and the seeded
+input generators; the GPU parity test reads the file.  Each form runs in
+about an hour on 8 CPU threads and needs about 13 GB of memory.
 
-    python tests/golden/make_layered512_full_run.py
+    python tests/golden/make_layered512_full_run.py [plain|staggered|density|local]
 """
 import os
 import sys
@@ -20,8 +22,18 @@ sys.path.insert(0, ROOT)
 from oracle import oracle as O  # noqa: E402
 from paper_2606_06910_gb300 import synth  # noqa: E402
 
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "layered512_full_run.txt")
 EVERY = 10
+FORMS = ("plain", "staggered", "density", "local")
+
+
+def out_path(form):
+    name = "layered512_full_run.txt" if form == "plain" else f"layered512_full_run_{form}.txt"
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), name)
+
+
+def form_dt(w, form):
+    """Time step of the form: the staggered limit is 0.4488, so it runs at 0.4."""
+    return 0.4 * w.h / w.vmax if form == "staggered" else w.dt
 
 
 def receivers_and_nodes(w):
@@ -39,23 +51,34 @@ def receivers_and_nodes(w):
     return rec, nodes
 
 
-def main():
+def main(form="plain"):
+    assert form in FORMS, form
+    OUT = out_path(form)
     w = synth.preset("layered512")
     rec, nodes = receivers_and_nodes(w)
-    vel = w.velocity().astype(np.float64)
-    g = O.Grid(vel * vel, w.h, w.dt, O.make_profiles(w.shape, w.cpml_cells, w.h, w.dt, w.vmax, R=w.R))
-    del vel
+    dt = form_dt(w, form)
+    vel32 = w.velocity()
+    vel = vel32.astype(np.float64)
+    prof = O.make_profiles(w.shape, w.cpml_cells, w.h, dt, w.vmax, R=w.R)
+    if form == "density":
+        rho = ((vel32 / np.float32(1500.0)) ** np.float32(0.25)).astype(np.float64)   # the library's FP32 input
+        g = O.Grid(rho * vel * vel, w.h, dt, prof, rho=rho)
+    elif form == "local":
+        g = O.Grid(vel * vel, w.h, dt, prof, local=O.local_profiles(vel, w.cpml_cells, w.h, dt, R=w.R))
+    else:
+        g = O.Grid(vel * vel, w.h, dt, prof, staggered=form == "staggered")
+    del vel, vel32
     st = O.State(w.shape)
     src = tuple(int(v) for v in w.sources()[0])
-    wav = w.wavelet()[0].astype(np.float64)
+    wav = synth.ricker(w.nt, dt, w.f0).astype(np.float32).astype(np.float64)
     t0 = time.time()
     traces = O.run(g, st, w.nt, 0, src, wav, rec)
     secs = time.time() - t0
     p = st["p"]
     with open(OUT + ".tmp", "w") as f:
         f.write("# FP64 oracle, full run of the 512^3 layered workload (Sec. 3.1 leapfrog, Sec. 3.2 CPML):\n")
-        f.write(f"# {w.nt} steps, dt = {w.dt!r}, h = {w.h}, 20-cell CPML, R = {w.R}, c_ref = {w.vmax}, "
-                f"10 Hz Ricker at {src}.\n")
+        f.write(f"# form {form}; {w.nt} steps, dt = {dt!r}, h = {w.h}, 20-cell CPML, R = {w.R}, "
+                f"c_ref = {w.vmax}, 10 Hz Ricker at {src}.\n")
         f.write(f"# Written by tests/golden/make_layered512_full_run.py ({secs:.0f} s).\n")
         f.write("# R z y x: receivers, in column order of the T lines\n")
         f.write(f"# T n v...: p at the receivers after step n (every {EVERY}th step)\n")
@@ -71,4 +94,4 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1] if len(sys.argv) > 1 else "plain")
