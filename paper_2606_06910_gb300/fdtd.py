@@ -142,7 +142,8 @@ class Fdtd:
 
     def set_staggered(self, on: bool = True):
         """Staggered (Yee) form: v_d at the half nodes i + 1/2, staggered
-        radius-4 derivatives; FP32 storage, constant density, forward only."""
+        radius-4 derivatives; FP32 storage and constant density.  adjoint()
+        transposes it (grad_cpml is not provided for it)."""
         self._check(self.lib.fdtd_set_staggered(self.ctx, 1 if on else 0))
 
     def set_cpml_ska(self, ska: torch.Tensor):
@@ -173,6 +174,11 @@ class Fdtd:
         self._check(self.lib.fdtd_step_n(self.ctx, int(n)))
 
     def adjoint(self, n, resid=None, grad_vel=None, grad_cpml=None):
+        """The discrete adjoint of the last n (= current time) steps from the
+        checkpoints: resid [nshots, nt_max, nrec] is injected at the
+        receivers; grad_vel [nz, ny, nx] receives += dJ/dc summed over shots;
+        grad_cpml [3, 3, max(shape)] receives += dJ/d(b, a, 1/kappa) (needs
+        cpml_grad=True; collocated form with the 1D grading only)."""
         if resid is not None:
             _need(resid, (self.nshots, self.nt_max, self.nrec), self.device, "resid")
         if grad_vel is not None:
