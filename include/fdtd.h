@@ -207,12 +207,17 @@ int fdtd_set_cpml_ska(fdtd_ctx *ctx, const float *ska_dev);
 /* Source per shot: src_zyx (host int [nshots][3]) and wavelet_dev (dev float
  * [nshots][nt], copied).  After the pressure update of step n, w[shot][n] is
  * added to p at the source node (additive pressure source; samples n >= nt
- * add nothing).  EINVAL if a node is outside the grid or nt > nt_max. */
+ * add nothing).  The paper gives only the source's time function, the Ricker
+ * pulse of Sec. 4.2 (the caller samples it, w[n] = s(n dt)); how it enters the
+ * update is left open, and this additive injection after the pressure step,
+ * with the amplitude as given, is the reading taken here and by the oracle.  EINVAL if a node is outside the grid or nt > nt_max. */
 int fdtd_inject(fdtd_ctx *ctx, const int *src_zyx, const float *wavelet_dev, int nt);
 
 /* Receivers, shared by all shots: rec_zyx (host int [nrec][3]).  After the
  * source of step n, traces_dev[shot][n][r] = p at receiver r for every
- * n < nt_max (traces_dev: dev float [nshots][nt_max][nrec], written in
+ * n < nt_max (the paper samples no receivers; its Sec. 4.2 reflection ratios
+ * compare the pressure at fixed nodes, and sampling p^{n+1} after the source
+ * of step n is the reading taken here and by the oracle) (traces_dev: dev float [nshots][nt_max][nrec], written in
  * place).  nrec = 0 disables recording.  EINVAL if a node is outside the
  * grid or nrec > nrec_max. */
 int fdtd_record(fdtd_ctx *ctx, const int *rec_zyx, int nrec, float *traces_dev);
@@ -269,11 +274,17 @@ int fdtd_time(const fdtd_ctx *ctx, int *t);
 int fdtd_sync(fdtd_ctx *ctx);
 
 /* sum of p^2 over the box [z0,z1) x [y0,y1) x [x0,x1) of one shot, accumulated
- * in FP64 on the device; box = {z0, z1, y0, y1, x0, x1}.  Synchronises. */
+ * in FP64 on the device; box = {z0, z1, y0, y1, x0, x1}.  Synchronises.
+ * This is the "normalized field energy" of the paper's CPML demonstration
+ * (Sec. 4.2, energy-decay figure), read as the sum of p^2 over a box, to be
+ * normalised by its peak over time by the caller. */
 int fdtd_energy(fdtd_ctx *ctx, int shot, const int box[6], double *out);
 
 /* Data misfit J = 1/2 sum (traces - dobs)^2 over [nshots][nt][nrec] of the
- * recorded traces (first nt steps), accumulated in FP64 on the device;
+ * recorded traces (first nt steps), accumulated in FP64 on the device.  The
+ * paper has no inversion; this L2 misfit is the objective whose gradient
+ * fdtd_adjoint_step_n computes (resid is its dJ/dtrace), and Sec. 4.1's
+ * relative L2 error is the same norm;
  * resid_dev (nullable, dev float [nshots][nt_max][nrec]) receives
  * traces - dobs for n < nt and 0 beyond.  dobs_dev: dev float
  * [nshots][nt_max][nrec].  Synchronises. */
@@ -295,10 +306,12 @@ int fdtd_misfit(fdtd_ctx *ctx, const float *dobs_dev, int nt, float *resid_dev, 
  *   cudaStream_t (NULL = default).  Synchronises the stream.
  *   EINVAL if a pointer is NULL or n is outside [1, FDTD_NOALLOC_MISFIT_MAX];
  *   ECUDA if a CUDA call fails.
- * The first call on a device looks up the scratch array's device address
- * (set-up); make that first call before any stream capture.  All calls on a
- * device share the scratch array, so calls that overlap on the GPU (e.g. on
- * two streams at once) race and must be serialised by the caller. */
+ * Every call looks up the scratch array's device address on the current
+ * device (a host-side query); the first call on a device also loads the
+ * library's device code there, its set-up, so make that first call before any
+ * stream capture begins on the device.  All calls on a device share the
+ * scratch array, so calls that overlap on the GPU (e.g. on two streams at
+ * once) race and must be serialised by the caller. */
 int fdtd_misfit_noalloc(const float *traces_dev, const float *dobs_dev, long long n, float *resid_dev,
                         double *out_host, void *stream);
 

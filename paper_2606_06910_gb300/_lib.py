@@ -21,6 +21,9 @@ OK, EINVAL, ENOMEM, ECUDA, ESTATE, EUNSTABLE, EDIVERGED, ETIMEOUT, EUNSUPPORTED 
 STATUS_NAMES = {0: "FDTD_OK", 1: "FDTD_EINVAL", 2: "FDTD_ENOMEM", 3: "FDTD_ECUDA", 4: "FDTD_ESTATE",
                 5: "FDTD_EUNSTABLE", 6: "FDTD_EDIVERGED", 7: "FDTD_ETIMEOUT", 8: "FDTD_EUNSUPPORTED"}
 
+# FDTD_NOALLOC_MISFIT_MAX: largest n of fdtd_misfit_noalloc
+NOALLOC_MISFIT_MAX = 4096 * 65536
+
 # fdtd_storage
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 

@@ -10,13 +10,15 @@
 // the process exits.
 //
 // The array's name in host code is a host-side stand-in, not a device address,
-// so the host looks the device address up with cudaGetSymbolAddress once per
-// device (with that device current) and passes it to the kernels.  All calls
-// on a device share the array; the kernels overwrite every partial they later
-// read, so nothing has to start at zero, but calls that overlap on the GPU
-// (concurrent streams) race on it.
-#include <mutex>
-
+// so every call looks the device address up with cudaGetSymbolAddress on the
+// caller's current device and passes it to the kernels.  The lookup is a
+// host-side query; the first one on a device also loads the library's device
+// code there (the set-up of that device).  Looking it up on every call, rather
+// than caching it, keeps the address right after a context teardown
+// (cudaDeviceReset) reloads the module.  All calls on a device share the
+// array; the kernels overwrite every partial they later read, so nothing has
+// to start at zero, but calls that overlap on the GPU (concurrent streams)
+// race on it.
 #include "fdtd_internal.cuh"
 
 namespace fdtd {
@@ -28,33 +30,19 @@ namespace {
 
 constexpr int kMaxBlocks = 4096;                       // partial sums
 constexpr long long kPerBlock = 65536;                 // values per partial
-constexpr int kMaxDevices = 64;
 static_assert((long long)kMaxBlocks * kPerBlock == FDTD_NOALLOC_MISFIT_MAX, "limit mismatch");
 
 // kMaxBlocks partial sums followed by the result (33 KB)
 __device__ __align__(256) double g_misfit_scratch[kMaxBlocks + 32];
 
-std::mutex g_mu;
-double *g_scratch_addr[kMaxDevices];
-
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device.
 cudaError_t scratch_address(double **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_misfit_scratch);
     if (e != cudaSuccess)
         return e;
-    if (dev < 0 || dev >= kMaxDevices)
-        return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_misfit_scratch);
-        if (e != cudaSuccess)
-            return e;
-        g_scratch_addr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 

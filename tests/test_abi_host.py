@@ -130,3 +130,10 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.fdtd_set_anisotropy(None, None) == _lib.EINVAL
     assert lib.fdtd_set_model(None, None, None) == _lib.EINVAL
     assert lib.fdtd_adjoint_step_n(None, 0, None, None, None) == _lib.EINVAL
+
+
+def test_noalloc_limit_matches_header():
+    import re
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "fdtd.h")).read()
+    m = re.search(r"#define FDTD_NOALLOC_MISFIT_MAX (\d+)LL", hdr)
+    assert m and int(m.group(1)) == _lib.NOALLOC_MISFIT_MAX

@@ -57,3 +57,57 @@ def test_noalloc_misfit_rejects_bad_sizes():
     for n in (0, -5, (1 << 28) + 1):
         assert lib.fdtd_misfit_noalloc(p, p, ctypes.c_longlong(n), None, ctypes.byref(out), None) == _lib.EINVAL
     assert lib.fdtd_misfit_noalloc(None, p, ctypes.c_longlong(8), None, ctypes.byref(out), None) == _lib.EINVAL
+
+
+def _noalloc(lib, a, b, n, resid):
+    out = ctypes.c_double(-1.0)
+    st = lib.fdtd_misfit_noalloc(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), ctypes.c_longlong(n),
+                                 ctypes.c_void_p(resid.data_ptr()) if resid is not None else None,
+                                 ctypes.byref(out), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return st, out.value
+
+
+def _fp64_half_sum_sq(a, b, chunk=1 << 26):
+    """1/2 sum (a - b)^2 with the FP32 difference (the entry point's rounding)
+    squared and summed in FP64, in chunks to bound the temporaries."""
+    acc = 0.0
+    for i in range(0, a.numel(), chunk):
+        r = (a[i:i + chunk] - b[i:i + chunk]).double()
+        acc += float((r * r).sum())
+    return 0.5 * acc
+
+
+@pytest.mark.parametrize("n", [3 * 65536 + 17, 65536, 65537])
+def test_noalloc_misfit_several_partials(n):
+    # more than one partial sum (the grid-stride kernel's blocks, then the
+    # finishing block over them), with a ragged last block
+    lib = _lib.load()
+    g = torch.Generator(device="cuda").manual_seed(n)
+    a = torch.randn(n, device="cuda", generator=g)
+    b = torch.randn(n, device="cuda", generator=g)
+    ref = _fp64_half_sum_sq(a, b)
+    for _ in range(2):
+        resid = torch.full_like(a, 7.0)
+        st, J = _noalloc(lib, a, b, n, resid)
+        assert st == _lib.OK
+        assert abs(J - ref) <= 1e-12 * abs(ref), (J, ref)
+        assert torch.equal(resid, a - b)
+
+
+def test_noalloc_misfit_at_the_limit():
+    # n = FDTD_NOALLOC_MISFIT_MAX: every one of the 4096 partial slots in use
+    lib = _lib.load()
+    n = _lib.NOALLOC_MISFIT_MAX
+    g = torch.Generator(device="cuda").manual_seed(5)
+    a = torch.rand(n, device="cuda", generator=g)
+    b = torch.zeros(n, device="cuda")
+    b[::3] = 0.5
+    ref = _fp64_half_sum_sq(a, b)
+    for _ in range(2):
+        st, J = _noalloc(lib, a, b, n, None)
+        assert st == _lib.OK
+        assert abs(J - ref) <= 1e-11 * abs(ref), (J, ref)
+    st, _ = _noalloc(lib, a, b, n + 1, None)
+    assert st == _lib.EINVAL
+    del a, b
+    torch.cuda.empty_cache()
