@@ -48,11 +48,14 @@ def parse():
     ap.add_argument("--cells", type=int, default=None, help="override CPML cells per face (0: no CPML)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
+                    help="skip the 128^3 accuracy instance of the cpu_baseline leg")
     ap.add_argument("--forms-only", action="store_true", help="measure only the forms (profiling runs)")
     ap.add_argument("--variant", default="plain", choices=["plain", "staggered", "local", "density"],
                     help="form of the main line's step (profiling runs of the forms; FP32): the staggered grid "
                          "at CFL 0.4, the local-velocity CPML grading, or the density (c/1500)^(1/4)")
-    ap.add_argument("--forms", default="f16,bf16,adjoint,learned,tblock,density,aniso2d,staggered,local_cpml",
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--forms", default="f16,bf16,cpml_overhead,adjoint,learned,tblock,density,aniso2d,staggered,local_cpml",
                     help="comma list of forms measured after the main line ('' for none)")
     return ap.parse_args()
 
@@ -266,7 +269,7 @@ def run_ours(args, rank, world, local):
         vel_d = torch.empty_like(vel)
         wav_d = torch.empty_like(wav)
         snap_d = torch.empty(shape, dtype=torch.float32, device=dev)
-        ksteps = max(1, min(args.steps, 2))
+        ksteps = args.steps
         torch.cuda.synchronize(dev)
         e0 = time.perf_counter()
         for _ in range(ksteps):
@@ -335,8 +338,75 @@ def form_storage(storage, dev, nsteps=60, warm=10):
     torch.cuda.empty_cache()
     ach = bytes_launch * nsteps / secs / 1e9
     return {"workload": f"layered1024 {storage} storage, {nsteps} timed steps", "value": round(npts * nsteps / secs / 1e6, 1),
-            "unit": UNIT, "roofline_frac": round(ach / peak, 4), "achieved_GBps": round(ach, 1),
-            "accuracy": "vs FP64 oracle on the 128^3 instance: see tests/test_gpu_forms.py"}
+            "unit": UNIT, "roofline_frac": round(ach / peak, 4), "achieved_GBps": round(ach, 1)}
+
+
+ACCURACY_CHECKPOINTS = (250, 375, 500)
+
+
+def storage_accuracy_gpu(dev, storage):
+    """The precision form's 128^3 accuracy instance (same generator as the
+    1024^3 workload, seed 3, 500 steps) on the GPU: the pressure after steps
+    250, 375 and 500 and the receiver traces, as host arrays."""
+    import torch
+    from paper_2606_06910_gb300 import synth
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    w = synth.preset("layered128")
+    rec = synth.receiver_grid(w.shape, w.cpml_cells, 6, 6, w.cpml_cells[4])
+    sim = Fdtd(w.shape, w.h, w.dt, cpml_cells=w.cpml_cells, storage=storage, nt_max=w.nt, nrec_max=len(rec),
+               device=dev)
+    sim.set_model(torch.from_numpy(w.velocity()).to(dev))
+    sim.set_cpml(R=w.R, c_ref=w.vmax)
+    sim.inject(w.sources(), torch.from_numpy(w.wavelet()).to(dev))
+    traces = sim.record(rec)
+    out, t = {}, 0
+    for c in ACCURACY_CHECKPOINTS:
+        sim.step(c - t)
+        t = c
+        out[c] = sim.get("p").cpu().numpy().astype(np.float64)
+    sim.sync()
+    out["traces"] = traces[0].cpu().numpy().astype(np.float64)
+    sim.close()
+    return out
+
+
+def form_cpml_overhead(dev, nsteps=96, warm=8):
+    """CPML overhead as the paper defines it (Sec. 5): (T_CPML - T_none) /
+    T_none, on the 512^3 layered workload with 20 cells per face and with
+    none, same grid, source and steps; both times are the step kernel's own
+    launch times from the library's CUDA events."""
+    import torch
+    from paper_2606_06910_gb300 import synth
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    w = synth.preset("layered512")
+    vel = torch.from_numpy(w.velocity()).to(dev)
+    npts = float(np.prod(w.shape))
+    peak, _ = measured_peaks()
+    out = {}
+    for name, cells in (("cpml_20", w.cpml_cells), ("none", (0,) * 6)):
+        sim = Fdtd(w.shape, w.h, w.dt, cpml_cells=cells, nt_max=w.nt, device=dev)
+        sim.set_model(vel)
+        if any(cells):
+            sim.set_cpml(R=w.R, c_ref=w.vmax)
+        sim.inject(w.sources(), torch.from_numpy(w.wavelet()).to(dev))
+        sim.step(warm)
+        sim.sync()
+        sim.set_timing(True)
+        secs = _timed(sim.stream, lambda: sim.step(nsteps))
+        kms, nl = sim.timing("step")
+        b = algorithmic_bytes(w.shape, cells, 4)
+        out[name] = {"value": round(npts * nsteps / secs / 1e6, 1), "ms_per_step": round(secs / nsteps * 1e3, 4),
+                     "kernel_ms_per_launch": round(kms / nl, 4),
+                     "roofline_frac": round(b / (kms / nl * 1e-3) / 1e9 / peak, 4)}
+        del sim
+        torch.cuda.empty_cache()
+    t1, t0 = out["cpml_20"]["kernel_ms_per_launch"], out["none"]["kernel_ms_per_launch"]
+    b1 = algorithmic_bytes(w.shape, w.cpml_cells, 4)
+    b0 = algorithmic_bytes(w.shape, (0,) * 6, 4)
+    return {"workload": f"layered512, 20 CPML cells vs none, {warm} + {nsteps} timed steps", "unit": UNIT, **out,
+            "overhead": round((t1 - t0) / t0, 4),
+            "byte_floor": round((b1 - b0) / b0, 4),
+            "target": 0.03}
 
 
 def form_tblock(dev, nsteps=96, warm=8):
@@ -505,15 +575,34 @@ def form_adjoint(dev, nt=800, nshots=None, every=None):
     resid = torch.empty_like(sim.traces)
     t_fwd = _timed(sim.stream, lambda: sim.step(nt))
     J = sim.misfit(dobs, nt=nt, resid=resid)
+    sim.set_timing(True)
     t_adj = _timed(sim.stream, lambda: sim.adjoint(nt, resid, grad))
+    adj_ms, adj_n = sim.timing("adjoint")
+    rec_ms, rec_n = sim.timing("step")
     sim.sync()
     ok = bool(torch.isfinite(grad).all()) and float(grad.abs().max()) > 0
     pts = float(np.prod(w.shape)) * ns * nt
+    # fused adjoint kernel: read mu, lam_v (3), kdt, the taped bracket and
+    # dJ/dK, write mu, lam_v (3) and dJ/dK: 12 FP32 words per node and shot;
+    # plus the adjoint memory variables (read + write of two) per slab node
+    # and axis
+    nz, ny, nx = w.shape
+    cl = w.cpml_cells
+    slab = (cl[0] + cl[1]) * ny * nz + (cl[2] + cl[3]) * nx * nz + (cl[4] + cl[5]) * nx * ny
+    adj_bytes = ns * (48 * float(np.prod(w.shape)) + 16 * slab)
+    peak, kind = measured_peaks()
+    per_launch = adj_ms / max(adj_n, 1) * 1e-3
+    ach = adj_bytes / per_launch / 1e9
     del sim
     torch.cuda.empty_cache()
     return {"workload": f"adjoint256: 256^3 x {ns} shots x {nt} steps, C={every}", "value": round(pts / (t_fwd + t_adj) / 1e6, 1),
             "unit": UNIT + " (forward + adjoint)", "forward_s": round(t_fwd, 3), "adjoint_s": round(t_adj, 3),
-            "misfit": J, "gradient_finite_nonzero": ok}
+            "misfit": J, "gradient_finite_nonzero": ok,
+            "recompute_step_launches": rec_n, "recompute_ms_per_launch": round(rec_ms / max(rec_n, 1), 4),
+            "roofline": {"bound": "hbm", "kernel": "adj_fused_kernel", "launches": adj_n,
+                         "avg_launch_us": round(per_launch * 1e6, 2), "algorithmic_bytes_per_launch": int(adj_bytes),
+                         "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                         "peak_source": f"{kind} hbm_gbs"}}
 
 
 def form_learned(dev, iters=30):
@@ -603,8 +692,73 @@ def oracle_sample(preset: str, nsteps: int, warm: int = 0):
     t = time.perf_counter()
     O.run(g, st, nsteps, warm, src, wav)
     dt = time.perf_counter() - t
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return float(np.prod(w.shape)) * nsteps / dt / 1e6, dt, threads
+    return float(np.prod(w.shape)) * nsteps / dt / 1e6, dt, int(O.threads())
+
+
+def physical_cores() -> int:
+    """Distinct (package, core) pairs of the host's CPUs (logical CPUs when
+    the topology is not readable)."""
+    import re
+    base, seen = "/sys/devices/system/cpu", set()
+    try:
+        for d in os.listdir(base):
+            if re.fullmatch(r"cpu\d+", d):
+                try:
+                    core = open(f"{base}/{d}/topology/core_id").read().strip()
+                    pkg = open(f"{base}/{d}/topology/physical_package_id").read().strip()
+                    seen.add((pkg, core))
+                except OSError:
+                    pass
+    except OSError:
+        pass
+    return len(seen) or (os.cpu_count() or 1)
+
+
+def oracle_sample_one_core(preset: str, nsteps: int = 1):
+    """The oracle on one thread, in a child process (OpenMP fixes its thread
+    count at load time): (Mpoints/s, seconds) or None."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", f"{preset}:{nsteps}"],
+                           env=env, capture_output=True, text=True, timeout=600)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return d["mpts"], d["secs"]
+    except Exception:
+        return None
+
+
+def oracle_accuracy_reference():
+    """The FP64 oracle on the precision form's 128^3 accuracy instance: the
+    pressure after each checkpoint and the traces (the same receivers as
+    storage_accuracy_gpu)."""
+    from oracle import oracle as O
+    from paper_2606_06910_gb300 import synth
+    w = synth.preset("layered128")
+    vel = w.velocity().astype(np.float64)
+    g = O.Grid(vel * vel, w.h, w.dt, O.make_profiles(w.shape, w.cpml_cells, w.h, w.dt, w.vmax, R=w.R))
+    st = O.State(w.shape)
+    src = tuple(w.sources()[0])
+    wav = w.wavelet()[0].astype(np.float64)
+    rec = synth.receiver_grid(w.shape, w.cpml_cells, 6, 6, w.cpml_cells[4])
+    out, t, trs = {}, 0, []
+    for c in ACCURACY_CHECKPOINTS:
+        trs.append(O.run(g, st, c - t, t, src, wav, rec))
+        t = c
+        out[c] = st["p"].copy()
+    out["traces"] = np.concatenate(trs)
+    return out
+
+
+def accuracy_line(gpu, ref, budget):
+    """Relative L2 of the GPU's pressure at each checkpoint and of its traces
+    against the oracle, with whether each meets the budget."""
+    def rl(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    e = {f"p_step{c}": rl(gpu[c], ref[c]) for c in ACCURACY_CHECKPOINTS}
+    e["traces"] = rl(gpu["traces"], ref["traces"])
+    return {"instance": "layered128 (seed 3), 500 steps, vs the FP64 oracle", "rel_l2": {k: float(f"{v:.4e}") for k, v in e.items()},
+            "budget": budget, "budget_met": {k: v <= budget for k, v in e.items()},
+            "budget_met_all": all(v <= budget for v in e.values())}
 
 
 def state_gb(shape, storage):
@@ -648,7 +802,7 @@ def run_reference(args, rank, world):
         O.run(g, st, 1, k, src, wav)
         if k >= args.warmup:
             times.append(time.perf_counter() - t)
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = int(O.threads())
     value = float(np.prod(w.shape)) * len(times) / sum(times) / 1e6
     sample = f"{args.preset} full grid, one FP64 oracle time step per bench step (OpenMP, {threads} threads)"
     return {
@@ -662,9 +816,45 @@ def run_reference(args, rank, world):
     }
 
 
+def cpu_baseline_leg(args, out, local):
+    """The FP64 oracle on the host cores, after every GPU measurement: the
+    timed sample of the workload (all threads, and one thread), and the
+    oracle's run of the precision form's 128^3 accuracy instance, against
+    which the FP32 path and the 16-bit forms report their relative L2 error."""
+    import oracle
+    from oracle import oracle as O
+    oracle.build()
+    nsamp = 8
+    mpts, secs, threads = oracle_sample(args.preset, nsamp, warm=1)
+    one = oracle_sample_one_core(args.preset, 1)
+    line = {"value": round(mpts, 3), "unit": UNIT, "cores": int(O.threads()), "kind": "oracle",
+            "sample": f"{args.preset} full grid, {nsamp} FP64 oracle time steps after 1 untimed ({secs:.1f} s)",
+            "logical_cpus": os.cpu_count(), "physical_cores": physical_cores()}
+    if one is not None:
+        line["one_thread"] = {"value": round(one[0], 3), "unit": UNIT,
+                              "sample": f"{args.preset} full grid, 1 FP64 oracle time step on one thread ({one[1]:.1f} s)"}
+    forms = out.get("forms", {})
+    if args.accuracy and "value" in out:
+        import torch
+        dev = torch.device("cuda", local)
+        t0 = time.perf_counter()
+        ref = oracle_accuracy_reference()
+        line["accuracy_reference_s"] = round(time.perf_counter() - t0, 1)
+        out["accuracy"] = accuracy_line(storage_accuracy_gpu(dev, "f32"), ref, 1e-4)
+        for st in ("f16", "bf16"):
+            if st in forms and "error" not in forms[st]:
+                forms[st]["accuracy"] = accuracy_line(storage_accuracy_gpu(dev, st), ref, 2e-2)
+    return line
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.oracle_sample:
+        preset, n = args.oracle_sample.split(":")
+        mpts, secs, threads = oracle_sample(preset, int(n))
+        print(json.dumps({"mpts": mpts, "secs": secs, "threads": threads}), flush=True)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:
@@ -692,6 +882,8 @@ def main():
                     forms[f] = form_adjoint(dev, nt=int(nt), nshots=int(ns), every=int(nt))
                 elif f == "learned":
                     forms[f] = form_learned(dev)
+                elif f == "cpml_overhead":
+                    forms[f] = form_cpml_overhead(dev)
                 elif f == "tblock":
                     forms[f] = form_tblock(dev)
                 elif f == "density":
@@ -711,13 +903,7 @@ def main():
         return
     if rank == 0:
         if not args.no_cpu_baseline:
-            import oracle
-            oracle.build()
-            nsamp = 8
-            mpts, secs, threads = oracle_sample(args.preset, nsamp, warm=1)
-            out["cpu_baseline"] = {"value": round(mpts, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
-                                   "sample": f"{args.preset} full grid, {nsamp} FP64 oracle time steps after "
-                                             f"1 untimed ({secs:.1f} s)"}
+            out["cpu_baseline"] = cpu_baseline_leg(args, out, local)
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

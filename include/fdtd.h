@@ -290,6 +290,28 @@ int fdtd_energy(fdtd_ctx *ctx, int shot, const int box[6], double *out);
  * [nshots][nt_max][nrec].  Synchronises. */
 int fdtd_misfit(fdtd_ctx *ctx, const float *dobs_dev, int nt, float *resid_dev, double *out);
 
+/* Kernel classes of fdtd_timing. */
+typedef enum {
+    FDTD_TIMING_STEP = 0,     /* the fused forward step kernel (also its recompute launches in the adjoint) */
+    FDTD_TIMING_ADJOINT = 1   /* the adjoint step: the fused adjoint kernel (node-per-thread kernels with grad_cpml) */
+} fdtd_timing_class;
+
+/* Device-side timing of the library's kernels (the CUDA events per step of
+ * the measurement plan; the paper times whole runs by wall clock, Sec. 5).
+ * on != 0 records a CUDA event pair around every launch of each kernel class
+ * on the stream it is launched on, and clears the totals; on = 0 stops
+ * recording (totals are kept).  Events are created on the first call with
+ * on != 0 and destroyed with the context.  Every 4096 launches of a class
+ * the host waits for the launches recorded so far (a synchronisation), so
+ * timing is meant for measurement runs. */
+int fdtd_set_timing(fdtd_ctx *ctx, int on);
+
+/* Milliseconds of device time and number of launches of one kernel class
+ * (fdtd_timing_class) since timing was switched on: the sum over launches of
+ * each launch's own start-to-end event interval.  Synchronises the stream
+ * (and the temporal-blocking streams).  EINVAL for an unknown class. */
+int fdtd_timing(fdtd_ctx *ctx, int kernel_class, double *ms, long long *launches);
+
 /* Largest n accepted by fdtd_misfit_noalloc: 4096 partial sums of 65536 values. */
 #define FDTD_NOALLOC_MISFIT_MAX 268435456LL
 

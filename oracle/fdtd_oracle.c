@@ -444,3 +444,12 @@ void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
 
 /* Layout version of og_grid/og_state; the Python side checks it on load. */
 long og_version(void) { return 1; }
+
+/* Threads an OpenMP loop of this library uses (1 when built without OpenMP);
+ * reported next to timings of the oracle. */
+#ifdef _OPENMP
+#include <omp.h>
+long og_threads(void) { return omp_get_max_threads(); }
+#else
+long og_threads(void) { return 1; }
+#endif

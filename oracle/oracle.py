@@ -381,6 +381,13 @@ class Grid:
         return g
 
 
+def threads() -> int:
+    """OpenMP threads the C core's loops use."""
+    f = _clib().og_threads
+    f.restype = ctypes.c_long
+    return int(f())
+
+
 def velocity_stage(grid: Grid, st: State):
     """Velocity half step (Sec. 3.1 leapfrog, Sec. 3.2 CPML velocity update)."""
     c = st._c()

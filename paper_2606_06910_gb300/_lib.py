@@ -24,6 +24,9 @@ STATUS_NAMES = {0: "FDTD_OK", 1: "FDTD_EINVAL", 2: "FDTD_ENOMEM", 3: "FDTD_ECUDA
 # FDTD_NOALLOC_MISFIT_MAX: largest n of fdtd_misfit_noalloc
 NOALLOC_MISFIT_MAX = 4096 * 65536
 
+# fdtd_timing_class
+TIMING_STEP, TIMING_ADJOINT = 0, 1
+
 # fdtd_storage
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 
@@ -68,6 +71,8 @@ _SIGS = {
     "fdtd_misfit": (c_int, [c_void_p, c_void_p, c_int, c_void_p, ctypes.POINTER(c_double)]),
     "fdtd_misfit_noalloc": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_void_p,
                                     ctypes.POINTER(c_double), c_void_p]),
+    "fdtd_set_timing": (c_int, [c_void_p, c_int]),
+    "fdtd_timing": (c_int, [c_void_p, c_int, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "fdtd_cpml_ska_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "fdtd_mlp_forward": (c_int, [c_void_p, c_void_p, c_int, c_float, c_float, c_void_p, c_void_p, c_void_p]),
     "fdtd_mlp_backward": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_float, c_float,

@@ -448,8 +448,59 @@ int make_tblock(fdtd_ctx *c)
     return FDTD_OK;
 }
 
+// ---- kernel timing (fdtd_set_timing) ----
+constexpr int kTimingPairs = 4096;
+
+// Fold the recorded pairs of class k into the totals (waits for them).
+cudaError_t timing_fold(fdtd_ctx *c, int k)
+{
+    for (int i = 0; i < c->tev_used[k]; ++i) {
+        cudaError_t e = cudaEventSynchronize(c->tev[k][2 * i + 1]);
+        if (e != cudaSuccess)
+            return e;
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, c->tev[k][2 * i], c->tev[k][2 * i + 1]);
+        if (e != cudaSuccess)
+            return e;
+        c->t_ms[k] += ms;
+    }
+    c->t_launch[k] += c->tev_used[k];
+    c->tev_used[k] = 0;
+    return cudaSuccess;
+}
+
+// Event before a launch of class k on `st` (no-op unless timing is on).
+cudaError_t timing_begin(fdtd_ctx *c, int k, cudaStream_t st)
+{
+    if (!c->timing)
+        return cudaSuccess;
+    if (c->tev_used[k] == kTimingPairs) {
+        const cudaError_t e = timing_fold(c, k);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaEventRecord(c->tev[k][2 * c->tev_used[k]], st);
+}
+
+// Event after that launch.
+cudaError_t timing_end(fdtd_ctx *c, int k, cudaStream_t st)
+{
+    if (!c->timing)
+        return cudaSuccess;
+    const cudaError_t e = cudaEventRecord(c->tev[k][2 * c->tev_used[k] + 1], st);
+    c->tev_used[k] += 1;
+    return e;
+}
+
 void free_ctx(fdtd_ctx *c)
 {
+    for (int k = 0; k < 2; ++k)
+        if (c->tev[k]) {
+            for (int i = 0; i < 2 * kTimingPairs; ++i)
+                if (c->tev[k][i])
+                    cudaEventDestroy(c->tev[k][i]);
+            delete[] c->tev[k];
+        }
     if (c->tb_ev) {
         for (size_t i = 0; i < (size_t)c->d.tblock_k * c->tb_nb; ++i)
             if (c->tb_ev[i])
@@ -572,7 +623,9 @@ int launch_blocks(fdtd_ctx *c, int m)
                     a.psiv_in[d] = c->psiv[d][set];
                     a.psiv_out[d] = c->psiv[d][set ^ 1];
                 }
+                CUDA_TRY(c, timing_begin(c, FDTD_TIMING_STEP, st));
                 CUDA_TRY(c, launch_step(c, a, set, st));
+                CUDA_TRY(c, timing_end(c, FDTD_TIMING_STEP, st));
                 CUDA_TRY(c, cudaEventRecord(ev(s, b), st));
             }
         c->cur = (c->cur + k) & 1;
@@ -600,7 +653,9 @@ int launch_one_step(fdtd_ctx *c, bool record, float *s_tape, float *const slab_t
     if (!record)
         a.traces = nullptr;
     a.s_tape = s_tape;
+    CUDA_TRY(c, timing_begin(c, FDTD_TIMING_STEP, c->stream));
     CUDA_TRY(c, launch_step(c, a, s, c->stream));
+    CUDA_TRY(c, timing_end(c, FDTD_TIMING_STEP, c->stream));
     c->cur ^= 1;
     c->t += 1;
     return FDTD_OK;
@@ -1180,10 +1235,12 @@ int fdtd_adjoint_step_n(fdtd_ctx *c, int n, const float *resid, float *grad_vel,
                                           : nullptr;
             const float *sk = c->tape_s + (size_t)(k - s0) * c->d.nshots * c->g.vol;
             // the fused kernel carries no profile gradient; that path keeps the node-per-thread kernels
+            CUDA_TRY(c, timing_begin(c, FDTD_TIMING_ADJOINT, c->stream));
             if (want_prof)
                 CUDA_TRY(c, adjoint_step(c, sk, slab, true));
             else
                 CUDA_TRY(c, adjoint_step_fused(c, sk));
+            CUDA_TRY(c, timing_end(c, FDTD_TIMING_ADJOINT, c->stream));
         }
     }
     if (grad_vel)
@@ -1340,6 +1397,43 @@ int fdtd_sync(fdtd_ctx *c)
         return fail(c, FDTD_ETIMEOUT, "a bounded device-side wait gave up");
     if (err & ERR_NONFINITE)
         return fail(c, FDTD_EDIVERGED, "non-finite values");
+    return FDTD_OK;
+}
+
+int fdtd_set_timing(fdtd_ctx *c, int on)
+{
+    if (!c)
+        return FDTD_EINVAL;
+    if (on) {
+        for (int k = 0; k < 2; ++k) {
+            if (!c->tev[k]) {
+                c->tev[k] = new (std::nothrow) cudaEvent_t[2 * kTimingPairs]();
+                if (!c->tev[k])
+                    return fail(c, FDTD_ENOMEM, "timing events: host allocation failed");
+                for (int i = 0; i < 2 * kTimingPairs; ++i)
+                    CUDA_TRY(c, cudaEventCreate(&c->tev[k][i]));
+            }
+            CUDA_TRY(c, timing_fold(c, k));
+            c->t_ms[k] = 0.0;
+            c->t_launch[k] = 0;
+        }
+    }
+    c->timing = on != 0;
+    return FDTD_OK;
+}
+
+int fdtd_timing(fdtd_ctx *c, int kernel_class, double *ms, long long *launches)
+{
+    if (!c)
+        return FDTD_EINVAL;
+    if (kernel_class < 0 || kernel_class > 1)
+        return fail(c, FDTD_EINVAL, "unknown kernel class %d", kernel_class);
+    if (c->tev[kernel_class])
+        CUDA_TRY(c, timing_fold(c, kernel_class));
+    if (ms)
+        *ms = c->t_ms[kernel_class];
+    if (launches)
+        *launches = c->t_launch[kernel_class];
     return FDTD_OK;
 }
 

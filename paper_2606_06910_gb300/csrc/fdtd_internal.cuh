@@ -396,5 +396,13 @@ struct fdtd_ctx {
     cudaStream_t tb_stream[4];
     cudaEvent_t *tb_ev;     // [tblock_k][tb_nb]
     cudaEvent_t tb_entry;
+    // kernel timing (fdtd_set_timing): a pool of CUDA event pairs per kernel
+    // class, recorded around each launch on its stream and folded into the
+    // totals when the pool fills or the totals are read
+    bool timing;
+    cudaEvent_t *tev[2];    // [2 * kTimingPairs] per class, created on first use
+    int tev_used[2];        // pairs recorded and not yet folded
+    double t_ms[2];
+    long long t_launch[2];
     char last_error[256];
 };

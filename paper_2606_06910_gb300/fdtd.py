@@ -200,6 +200,18 @@ class Fdtd:
     def sync(self):
         self._check(self.lib.fdtd_sync(self.ctx))
 
+    # -- kernel timing (CUDA events around each launch, in the library) -------
+    def set_timing(self, on: bool = True):
+        self._check(self.lib.fdtd_set_timing(self.ctx, 1 if on else 0))
+
+    def timing(self, kernel: str = "step"):
+        """(milliseconds, launches) of the step or adjoint kernels since
+        set_timing(True)."""
+        ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
+        k = {"step": _lib.TIMING_STEP, "adjoint": _lib.TIMING_ADJOINT}[kernel]
+        self._check(self.lib.fdtd_timing(self.ctx, k, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
     # -- fields ------------------------------------------------------------
     def get(self, which: str, shot=0, out: torch.Tensor | None = None) -> torch.Tensor:
         if out is None:
