@@ -337,6 +337,15 @@ int fdtd_timing(fdtd_ctx *ctx, int kernel_class, double *ms, long long *launches
 int fdtd_misfit_noalloc(const float *traces_dev, const float *dobs_dev, long long n, float *resid_dev,
                         double *out_host, void *stream);
 
+/* Per-cell (sigma, kappa, alpha) of the polynomial grading of Sec. 3.2 /
+ * Tab. 2 for a layer of L cells (the formulas of fdtd_set_cpml, in double on
+ * the host): ska_host double [L][3], cell j = 0 outermost at normalised depth
+ * (L - j)/L.  The learned CPML's fallback and the target of its pre-fit; the
+ * layout of fdtd_set_cpml_ska.  Needs no context and no GPU.  EINVAL for L
+ * outside [1, 1024], h or c_ref <= 0, or parameters as in fdtd_set_cpml. */
+int fdtd_cpml_grading(int L, double h, double c_ref, double R, double kappa_max, double alpha_frac,
+                      int q, double *ska_host);
+
 /* Chain rule of the learned CPML: from grad_cpml (layout of
  * fdtd_adjoint_step_n) and the per-cell ska_dev [L][3] given to
  * fdtd_set_cpml_ska, write gska_dev [L][3] = dJ/d(sigma, kappa, alpha). */
@@ -356,6 +365,14 @@ int fdtd_mlp_forward(const float *theta, const float *X, int n, float sigma_scal
 int fdtd_mlp_backward(const float *theta, const float *X, int n, const float *act,
                       const float *gout, float sigma_scale, float alpha_scale,
                       float *gtheta, void *stream);
+/* Gradient of the learned grading's pre-fit loss (fitting the network to a
+ * target grading, e.g. fdtd_cpml_grading's):
+ *   loss = sum_j [((sigma_j - s*_j)/sigma_scale)^2 + (kappa_j - k*_j)^2 + ((alpha_j - a*_j)/alpha_scale)^2],
+ * out, target: dev float [n][3] (sigma, kappa, alpha); gout: dev float [n][3]
+ * = dloss/dout; loss: dev float [1] or NULL.  Summed in double; one block on
+ * `stream`; n <= 1024. */
+int fdtd_mlp_fit_gradient(const float *out, const float *target, int n, float sigma_scale,
+                          float alpha_scale, float *gout, float *loss, void *stream);
 /* Adam (Kingma & Ba) on nparam values; step t >= 1. */
 int fdtd_adam_step(float *theta, const float *grad, float *m, float *v, int nparam, int t,
                    float lr, float beta1, float beta2, float eps, void *stream);

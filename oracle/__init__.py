@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-           "-shared", "-fPIC", "-o", tmp, _SRC]
+           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -55,6 +55,6 @@ def lib() -> ctypes.CDLL:
     if _lib is None:
         _lib = ctypes.CDLL(build())
         _lib.og_version.restype = ctypes.c_long
-        if _lib.og_version() != 1:
+        if _lib.og_version() != 2:
             raise RuntimeError("oracle C core layout version mismatch")
     return _lib

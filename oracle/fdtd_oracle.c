@@ -37,6 +37,7 @@
  *
  * Parity pins live in tests/test_oracle_*.py.
  */
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -60,7 +61,54 @@ typedef struct {
     const double *kinvv[3];
     const double *bn[3];      /* local grading: b_d per node [nz][ny][nx] (NULL: the 1D b[d]) */
     const double *an[3];      /* local grading: a_d per node (NULL: the 1D a[d]) */
+    /* 16-bit storage form: the arithmetic stays FP64, and every stored field
+     * is rounded to nearest (ties to even) in the storage format when it is
+     * written back: store_bits = 11 (FP16: 11-bit significand, normal
+     * exponents >= -14, largest finite 65504) or 8 (BF16: 8-bit significand,
+     * normal exponents >= -126); 0 = no rounding.  Fields are scaled before
+     * rounding as the form stores them: p and psi_v by scale_p, v and psi_p by
+     * scale_p * scale_v.  store_mask selects the fields rounded (bit 0 p,
+     * 1 v, 2 psi_v, 3 psi_p). */
+    int store_bits;
+    int store_mask;
+    double scale_p, scale_v;
 } og_grid;
+
+/* x rounded to the nearest value with a `bits`-bit significand whose
+ * exponent is at least emin (below it the quantum stays 2^(emin - bits + 1),
+ * the subnormal range), ties to even; beyond `fmax` the result is +-inf. */
+static double og_round_fmt(double x, int bits, int emin, double fmax)
+{
+    if (x == 0.0 || x != x)
+        return x;
+    int e;
+    frexp(x, &e);               /* |x| = m 2^e, m in [0.5, 1): exponent of the leading bit is e - 1 */
+    int lead = e - 1;
+    if (lead < emin)
+        lead = emin;
+    const double q = ldexp(1.0, lead - (bits - 1));
+    const double r = nearbyint(x / q) * q;   /* default rounding mode: to nearest, ties to even */
+    if (fabs(r) > fmax)
+        return x > 0 ? HUGE_VAL : -HUGE_VAL;
+    return r;
+}
+
+/* og_round_fmt for the two storage formats (bits = 11: FP16, 8: BF16); for tests. */
+double og_round16(double x, int bits)
+{
+    return bits == 11 ? og_round_fmt(x, 11, -14, 65504.0) : og_round_fmt(x, 8, -126, 3.3895313892515355e38);
+}
+
+/* A stored value of field class `cls` (bit of store_mask) in physical units. */
+static double og_store(const og_grid *g, int cls, double x)
+{
+    if (!g->store_bits || !(g->store_mask & (1 << cls)))
+        return x;
+    const double s = (cls == 0 || cls == 2) ? g->scale_p : g->scale_p * g->scale_v;
+    const double y = g->store_bits == 11 ? og_round_fmt(x * s, 11, -14, 65504.0)
+                                         : og_round_fmt(x * s, 8, -126, 3.3895313892515355e38);
+    return y / s;
+}
 
 /* CPML coefficients of axis d at node i (axis index k) */
 static double og_b(const og_grid *g, int d, long i, long k)
@@ -167,6 +215,7 @@ void og_velocity_stage(const og_grid *g, og_state *st)
                         const double a = g->staggered ? g->av[d][k] : og_a(g, d, i, k);
                         st->psiv[d][i] = b * st->psiv[d][i] + a * gd;
                         gd = kinv[k] * gd + st->psiv[d][i];
+                        st->psiv[d][i] = og_store(g, 2, st->psiv[d][i]);
                     }
                     st->v[d][i] -= g->dt / og_rho(g, i) * gd;
                 }
@@ -193,6 +242,7 @@ void og_pressure_stage(const og_grid *g, og_state *st, double *s_out)
                     if (g->slab[d][k]) {
                         st->psip[d][i] = og_b(g, d, i, k) * st->psip[d][i] + og_a(g, d, i, k) * hd;
                         hd = g->kinv[d][k] * hd + st->psip[d][i];
+                        st->psip[d][i] = og_store(g, 3, st->psip[d][i]);
                     }
                     s += g->kr[d] * hd;
                 }
@@ -200,6 +250,22 @@ void og_pressure_stage(const og_grid *g, og_state *st, double *s_out)
                 if (s_out)
                     s_out[i] = s;
             }
+}
+
+/*
+ * 16-bit storage form: p and v are written back rounded once the step's
+ * pressure update and source are done (the pressure update itself uses the
+ * unrounded new velocities, which a fused step keeps in registers).
+ */
+void og_store_state(const og_grid *g, og_state *st)
+{
+    long n = g->nx * g->ny * g->nz;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < n; i++) {
+        st->p[i] = og_store(g, 0, st->p[i]);
+        for (int d = 0; d < 3; d++)
+            st->v[d][i] = og_store(g, 1, st->v[d][i]);
+    }
 }
 
 /*
@@ -219,6 +285,8 @@ void og_run(const og_grid *g, og_state *st, long n0, long nsteps,
         og_pressure_stage(g, st, NULL);
         if (src && src[0] >= 0 && wavelet && n < nt_w)
             st->p[(src[0] * g->ny + src[1]) * g->nx + src[2]] += wavelet[n];
+        if (g->store_bits)
+            og_store_state(g, st);
         for (long r = 0; r < nrec; r++) {
             long z = rec[3 * r], y = rec[3 * r + 1], x = rec[3 * r + 2];
             traces[s * nrec + r] = st->p[(z * g->ny + y) * g->nx + x];
@@ -443,7 +511,7 @@ void og_adjoint_step(const og_grid *g, const og_state *fwd, og_state *adj,
 }
 
 /* Layout version of og_grid/og_state; the Python side checks it on load. */
-long og_version(void) { return 1; }
+long og_version(void) { return 2; }
 
 /* Threads an OpenMP loop of this library uses (1 when built without OpenMP);
  * reported next to timings of the oracle. */

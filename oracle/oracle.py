@@ -240,7 +240,8 @@ class _Grid(ctypes.Structure):
                 ("K", ctypes.c_void_p), ("b", _P3), ("a", _P3), ("kinv", _P3),
                 ("slab", _P3), ("rho_n", ctypes.c_void_p), ("kr", ctypes.c_double * 3),
                 ("staggered", ctypes.c_int), ("bv", _P3), ("av", _P3), ("kinvv", _P3),
-                ("bn", _P3), ("an", _P3)]
+                ("bn", _P3), ("an", _P3), ("store_bits", ctypes.c_int), ("store_mask", ctypes.c_int),
+                ("scale_p", ctypes.c_double), ("scale_v", ctypes.c_double)]
 
 
 class _State(ctypes.Structure):
@@ -317,7 +318,7 @@ class Grid:
     """
 
     def __init__(self, K, h, dt, profiles=None, rho=1.0, periodic=False, weights=None, kr=(1.0, 1.0, 1.0),
-                 staggered=False, local=None):
+                 staggered=False, local=None, store=None, store_mask=15, scale_p=1.0, scale_v=1.0):
         self.K = np.ascontiguousarray(K, dtype=np.float64)
         self.shape = self.K.shape
         self.h, self.dt = float(h), float(dt)
@@ -352,6 +353,13 @@ class Grid:
                 bv=np.ascontiguousarray(pr.get("bv", pr["b"]), dtype=np.float64),
                 av=np.ascontiguousarray(pr.get("av", pr["a"]), dtype=np.float64),
                 kinvv=np.ascontiguousarray(pr.get("kinvv", pr["kinv"]), dtype=np.float64)))
+        # the 16-bit storage form: FP64 arithmetic, stored fields rounded to
+        # FP16 / BF16 (bits of the significand 11 / 8) after scaling as the
+        # form stores them (see fdtd_oracle.c: og_store)
+        assert store in (None, "f16", "bf16")
+        self.store_bits = {None: 0, "f16": 11, "bf16": 8}[store]
+        self.store_mask = int(store_mask)
+        self.scale_p, self.scale_v = float(scale_p), float(scale_v)
         self._cg = self._make_c()
 
     def _make_c(self):
@@ -378,7 +386,23 @@ class Grid:
         g.rho_n = _ptr(self.rho_n) if self.rho_n is not None else None
         for d in range(3):
             g.kr[d] = self.kr[d]
+        g.store_bits, g.store_mask = self.store_bits, self.store_mask
+        g.scale_p, g.scale_v = self.scale_p, self.scale_v
         return g
+
+
+def store_state(grid: Grid, st: State):
+    """Round p and v as the 16-bit storage form writes them back at the end
+    of a step (no-op without ``store``)."""
+    _clib().og_store_state(ctypes.byref(grid._cg), ctypes.byref(st._c()))
+
+
+def round16(x: float, fmt: str) -> float:
+    """x rounded to nearest, ties to even, in FP16 or BF16 (as a double)."""
+    f = _clib().og_round16
+    f.restype = ctypes.c_double
+    f.argtypes = [ctypes.c_double, ctypes.c_int]
+    return float(f(float(x), 11 if fmt == "f16" else 8))
 
 
 def threads() -> int:

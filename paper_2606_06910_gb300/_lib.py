@@ -73,6 +73,8 @@ _SIGS = {
                                     ctypes.POINTER(c_double), c_void_p]),
     "fdtd_set_timing": (c_int, [c_void_p, c_int]),
     "fdtd_timing": (c_int, [c_void_p, c_int, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "fdtd_cpml_grading": (c_int, [c_int, c_double, c_double, c_double, c_double, c_double, c_int, c_void_p]),
+    "fdtd_mlp_fit_gradient": (c_int, [c_void_p, c_void_p, c_int, c_float, c_float, c_void_p, c_void_p, c_void_p]),
     "fdtd_cpml_ska_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "fdtd_mlp_forward": (c_int, [c_void_p, c_void_p, c_int, c_float, c_float, c_void_p, c_void_p, c_void_p]),
     "fdtd_mlp_backward": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_float, c_float,

@@ -30,6 +30,8 @@ cudaError_t launch_mlp_backward(const float *th, const float *X, int n, const fl
                                 float ssc, float asc, float *gth, cudaStream_t s);
 cudaError_t launch_adam(float *th, const float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps,
                         float c1, float c2, cudaStream_t s);
+cudaError_t launch_fit_gradient(const float *out, const float *tgt, int n, float ssc, float asc, float *gout,
+                                float *loss, cudaStream_t s);
 cudaError_t launch_adj_inject(const fdtd_ctx *c, const float *resid, int n);
 cudaError_t launch_grad_vel(const fdtd_ctx *c, float *grad_vel);
 cudaError_t adjoint_step(fdtd_ctx *c, const float *s_tape, float *const slab_tape[3], bool want_prof);
@@ -326,6 +328,20 @@ void choose_zchunk(fdtd_ctx *c)
 // nodes i + 1/2 of the staggered form, over the same slab index set: depth
 // (lo - i - 1/2)/lo on the low face, (i + 1/2 - (n - 1 - hi))/hi, at most 1,
 // on the high face.
+// Polynomial grading of Sec. 3.2 / Tab. 2 at normalised depth rho of a face
+// with L cells: sigma_max = -(q+1) c_ref ln R / (2 L h) (the continuous
+// layer's normal-incidence round trip is then R), sigma = sigma_max rho^q,
+// kappa = 1 + (kappa_max - 1) rho^q, alpha = alpha_frac sigma_max (1 - rho).
+void grading_ska(double rho, int L, double h, double R, double kmax, double afrac, int q, double cref,
+                 double *sigma, double *kappa, double *alpha)
+{
+    const double smax = -(q + 1) * cref * std::log(R) / (2.0 * L * h);
+    const double rq = std::pow(rho, q);
+    *sigma = smax * rq;
+    *kappa = 1.0 + (kmax - 1.0) * rq;
+    *alpha = afrac * smax * (1.0 - rho);
+}
+
 void host_profile(int n, int lo, int hi, double h, double dt, double R, double kmax, double afrac, int q, double cref,
                   bool half, float *b, float *a, float *kinv)
 {
@@ -349,11 +365,8 @@ void host_profile(int n, int lo, int hi, double h, double dt, double R, double k
             rho = i < lo ? double(lo - i) - 0.5 : std::min(double(hi), double(i - (n - 1 - hi)) + 0.5);
         if (half)
             rho /= L;
-        const double smax = -(q + 1) * cref * std::log(R) / (2.0 * L * h);
-        const double rq = std::pow(rho, q);
-        const double sigma = smax * rq;
-        const double kappa = 1.0 + (kmax - 1.0) * rq;
-        const double alpha = afrac * smax * (1.0 - rho);
+        double sigma, kappa, alpha;
+        grading_ska(rho, L, h, R, kmax, afrac, q, cref, &sigma, &kappa, &alpha);
         const double bb = std::exp(-(sigma / kappa + alpha) * dt);
         const double den = kappa * (sigma + kappa * alpha);
         b[i] = (float)bb;
@@ -1052,6 +1065,18 @@ int fdtd_set_cpml_ska(fdtd_ctx *c, const float *ska)
     return FDTD_OK;
 }
 
+int fdtd_cpml_grading(int L, double h, double c_ref, double R, double kappa_max, double alpha_frac, int q,
+                      double *ska)
+{
+    if (!ska || L < 1 || L > 1024 || !(h > 0.0) || !(c_ref > 0.0) || !(R > 0.0 && R <= 1.0) || !(kappa_max >= 1.0) ||
+        !(alpha_frac >= 0.0) || q < 0)
+        return FDTD_EINVAL;
+    for (int j = 0; j < L; ++j)
+        grading_ska(double(L - j) / L, L, h, R, kappa_max, alpha_frac, q, c_ref, &ska[3 * j], &ska[3 * j + 1],
+                    &ska[3 * j + 2]);
+    return FDTD_OK;
+}
+
 int fdtd_cpml_ska_backward(fdtd_ctx *c, const float *ska, const float *gprof, float *gska)
 {
     if (!c || !ska || !gprof || !gska)
@@ -1501,6 +1526,17 @@ int fdtd_adam_step(float *theta, const float *grad, float *m, float *v, int npar
     const float c1 = (float)(1.0 - std::pow((double)beta1, t));
     const float c2 = (float)(1.0 - std::pow((double)beta2, t));
     return launch_adam(theta, grad, m, v, nparam, lr, beta1, beta2, eps, c1, c2, (cudaStream_t)stream) == cudaSuccess
+               ? FDTD_OK
+               : FDTD_ECUDA;
+}
+
+int fdtd_mlp_fit_gradient(const float *out, const float *target, int n, float sigma_scale, float alpha_scale,
+                          float *gout, float *loss, void *stream)
+{
+    if (!out || !target || !gout || n < 1 || n > 1024 || !(sigma_scale > 0.f) || !(alpha_scale > 0.f))
+        return FDTD_EINVAL;
+    return launch_fit_gradient(out, target, n, sigma_scale, alpha_scale, gout, loss, (cudaStream_t)stream) ==
+                   cudaSuccess
                ? FDTD_OK
                : FDTD_ECUDA;
 }

@@ -552,6 +552,31 @@ cudaError_t launch_adam(float *th, const float *g, float *m, float *v, int n, fl
     return cudaGetLastError();
 }
 
+// Gradient of the pre-fit loss of the learned grading,
+//   loss = sum_j [((sigma_j - s*_j) / ss)^2 + (kappa_j - k*_j)^2 + ((alpha_j - a*_j) / as)^2],
+// with respect to the network outputs (one block; the loss summed in double).
+__global__ void fit_gradient_kernel(const float *out, const float *tgt, int n, float ssc, float asc, float *gout,
+                                    float *loss)
+{
+    const double w[3] = {1.0 / ((double)ssc * ssc), 1.0, 1.0 / ((double)asc * asc)};
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+        const double d = (double)out[i] - (double)tgt[i];
+        gout[i] = (float)(2.0 * d * w[i % 3]);
+        acc += d * d * w[i % 3];
+    }
+    const double sum = block_sum(acc);
+    if (threadIdx.x == 0 && loss)
+        *loss = (float)sum;
+}
+
+cudaError_t launch_fit_gradient(const float *out, const float *tgt, int n, float ssc, float asc, float *gout,
+                                float *loss, cudaStream_t s)
+{
+    fit_gradient_kernel<<<1, RED_THREADS, 0, s>>>(out, tgt, n, ssc, asc, gout, loss);
+    return cudaGetLastError();
+}
+
 int mlp_nparam() { return NPARAM; }
 int mlp_bwd_max() { return MLP_BWD_MAX; }
 

@@ -5,12 +5,15 @@ discrete adjoint on reflected energy.
 Downstream of (sigma, kappa, alpha) everything is the CPML of paper Sec. 3.2
 (b = exp(-(sigma/kappa + alpha) dt), a = sigma (b - 1) / (kappa (sigma + kappa
 alpha)), 1/kappa); the polynomial (Roden-Gedney) grading of Sec. 3.2 / Tab. 2
-is the fallback and the starting point.  All arithmetic runs in the library's
-kernels: network forward/backward and Adam (fdtd_mlp_*, fdtd_adam_step),
-coefficient map and its chain rule (fdtd_set_cpml_ska, fdtd_cpml_ska_backward),
-forward and adjoint wave propagation.  This module only marshals tensors.
+is the fallback and the starting point.  All arithmetic runs in the library:
+the polynomial grading (fdtd_cpml_grading), network forward/backward, the
+pre-fit loss gradient and Adam (fdtd_mlp_*, fdtd_adam_step), coefficient map
+and its chain rule (fdtd_set_cpml_ska, fdtd_cpml_ska_backward), forward and
+adjoint wave propagation, and the misfits (fdtd_misfit, fdtd_misfit_noalloc).
+This module builds the input features and marshals tensors.
 
-Features of layer cell j (j = 0 outermost of L cells):
+Features of layer cell j (j = 0 outermost of L cells), for a layer graded
+against the reference velocity c at time step dt and dominant frequency f0:
     [rho_j = (L - j)/L, L / L_ref, f0 h / c, c dt / h]
 Outputs: sigma = sigma_scale softplus(o0), kappa = 1 + softplus(o1),
 alpha = alpha_scale softplus(o2), sigma_scale = c / h, alpha_scale = pi f0.
@@ -25,39 +28,45 @@ import torch
 
 from . import _lib
 from ._lib import FdtdError
+from .synth import angled_sources, face_receivers, frequency_groups, mlp_init_params, ricker
 
 NPARAM = 4 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
 ACT = 2 * 64 + 3
 
 
 def _p(t):
-    return ctypes.c_void_p(t.data_ptr())
-
-
-def init_params(seed: int, scale1=0.5, scale2=0.2, scale3=0.1) -> np.ndarray:
-    """Seeded initial weights (normal, fixed scales), zero biases; float64."""
-    rng = np.random.default_rng(seed)
-    W1 = scale1 * rng.standard_normal((64, 4))
-    W2 = scale2 * rng.standard_normal((64, 64))
-    W3 = scale3 * rng.standard_normal((3, 64))
-    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), W3.ravel(), np.zeros(3)])
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
 def features(L: int, L_ref: int, f0: float, h: float, c: float, dt: float) -> np.ndarray:
+    """Network inputs of the L cells (see the module docstring)."""
     j = np.arange(L)
     return np.stack([(L - j) / L, np.full(L, L / L_ref), np.full(L, f0 * h / c), np.full(L, c * dt / h)],
                     axis=1)
 
 
-def roden_gedney_ska(L: int, h: float, c_ref: float, R: float = 1e-8, q: int = 3, kappa_max: float = 5.0,
-                     alpha_frac: float = 0.05) -> np.ndarray:
-    """Per-cell (sigma, kappa, alpha) of the polynomial grading of Sec. 3.2
-    (sigma_max = -(q+1) c_ref ln R / (2 L h)), cell j at depth rho = (L-j)/L."""
-    j = np.arange(L)
-    rho = (L - j) / L
-    smax = -(q + 1) * c_ref * math.log(R) / (2.0 * L * h)
-    return np.stack([smax * rho ** q, 1.0 + (kappa_max - 1.0) * rho ** q, alpha_frac * smax * (1.0 - rho)],
-                    axis=1)
+def polynomial_ska(L: int, h: float, c_ref: float, R: float = 1e-8, q: int = 3, kappa_max: float = 5.0,
+                   alpha_frac: float = 0.05) -> np.ndarray:
+    """Per-cell (sigma, kappa, alpha) [L, 3] of the polynomial grading of
+    Sec. 3.2 / Tab. 2, from the library (fdtd_cpml_grading)."""
+    lib = _lib.load()
+    out = (ctypes.c_double * (3 * L))()
+    st = lib.fdtd_cpml_grading(int(L), float(h), float(c_ref), float(R), float(kappa_max), float(alpha_frac),
+                               int(q), out)
+    if st != _lib.OK:
+        raise FdtdError(st, "fdtd_cpml_grading")
+    return np.frombuffer(out, dtype=np.float64).reshape(L, 3).copy()
+
+
+def misfit_flat(a: torch.Tensor, b: torch.Tensor) -> float:
+    """1/2 sum (a - b)^2 in FP64 on the device (fdtd_misfit_noalloc)."""
+    lib = _lib.load()
+    out = ctypes.c_double(0.0)
+    st = lib.fdtd_misfit_noalloc(_p(a), _p(b), ctypes.c_longlong(a.numel()), None, ctypes.byref(out),
+                                 ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream))
+    if st != _lib.OK:
+        raise FdtdError(st, "fdtd_misfit_noalloc")
+    return out.value
 
 
 class Network:
@@ -113,15 +122,20 @@ class LearnedCPML:
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
-        self.net = Network(init_params(seed) if theta is None else theta, self.device)
-        self.sigma_scale = c / h
-        self.alpha_scale = math.pi * f0
+        self.net = Network(mlp_init_params(seed) if theta is None else theta, self.device)
+        self.set_conditions(c, dt, f0)
+
+    def set_conditions(self, c: float, dt: float, f0: float):
+        """Reference velocity, time step and dominant frequency the layer is
+        graded for (the network's inputs and output scales)."""
+        self.c, self.dt = float(c), float(dt)
+        self.sigma_scale = self.c / self.h
         self.set_frequency(f0)
 
     def set_frequency(self, f0: float):
-        self.f0 = f0
-        self.alpha_scale = math.pi * f0
-        self.X = torch.tensor(features(self.L, self.L_ref, f0, self.h, self.c, self.dt).astype(np.float32),
+        self.f0 = float(f0)
+        self.alpha_scale = math.pi * self.f0
+        self.X = torch.tensor(features(self.L, self.L_ref, self.f0, self.h, self.c, self.dt).astype(np.float32),
                               device=self.device)
 
     def ska(self):
@@ -134,25 +148,37 @@ class LearnedCPML:
         (kappa - k*)^2 + ((alpha - a*)/alpha_scale)^2 with the library's
         backward and Adam kernels."""
         tgt = torch.tensor(np.asarray(target_ska, np.float32), device=self.device)
-        w = torch.tensor([1.0 / self.sigma_scale ** 2, 1.0, 1.0 / self.alpha_scale ** 2], device=self.device)
+        gout = torch.empty_like(tgt)
+        loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        lib, s = self.net.lib, self.net._s()
         for _ in range(iters):
             out, act = self.ska()
-            gout = 2.0 * (out - tgt) * w
+            st = lib.fdtd_mlp_fit_gradient(_p(out), _p(tgt), self.L, float(self.sigma_scale), float(self.alpha_scale),
+                                           _p(gout), _p(loss), s)
+            if st != _lib.OK:
+                raise FdtdError(st, "fdtd_mlp_fit_gradient")
             g = self.net.backward(self.X, act, gout, self.sigma_scale, self.alpha_scale)
             self.net.adam(g, lr)
         out, _ = self.ska()
-        return float((((out - tgt) ** 2) * w).sum())
+        st = lib.fdtd_mlp_fit_gradient(_p(out), _p(tgt), self.L, float(self.sigma_scale), float(self.alpha_scale),
+                                       _p(gout), _p(loss), s)
+        if st != _lib.OK:
+            raise FdtdError(st, "fdtd_mlp_fit_gradient")
+        return float(loss.item())
 
-    def gradient(self, sim, ref_traces: torch.Tensor, nt: int):
-        """J (reflected energy at the receivers: 1/2 sum (traces - ref)^2) and
-        dJ/dtheta for the current parameters, through one forward and one
-        adjoint run of `sim` (whose source and receivers are set)."""
+    def gradient(self, sim, ref_traces: torch.Tensor, nt: int, weight: float = 1.0):
+        """J (reflected energy at the receivers: weight * 1/2 sum (traces -
+        ref)^2 over the first nt steps) and dJ/dtheta for the current
+        parameters, through one forward and one adjoint run of `sim` (whose
+        source and receivers are set)."""
         out, act = self.ska()
         sim.reset()
         sim.set_cpml_ska(out)
         sim.step(nt)
         resid = torch.empty_like(ref_traces)
-        J = sim.misfit(ref_traces, nt=nt, resid=resid)
+        J = weight * sim.misfit(ref_traces, nt=nt, resid=resid)
+        if weight != 1.0:
+            resid.mul_(weight)
         gprof = torch.zeros((3, 3, max(sim.shape)), dtype=torch.float32, device=self.device)
         sim.adjoint(nt, resid, None, gprof)
         gska = sim.ska_backward(out, gprof)
@@ -160,101 +186,113 @@ class LearnedCPML:
         sim.reset()
         return J, g, out
 
-    def train_step(self, sim, ref_traces, nt, lr=2e-3):
-        J, g, out = self.gradient(sim, ref_traces, nt)
+    def train_step(self, sim, ref_traces, nt, lr=2e-3, weight=1.0):
+        J, g, out = self.gradient(sim, ref_traces, nt, weight)
         self.net.adam(g, lr)
         return J
 
 
-def _face_receivers(n: int, L: int, k: int, inset: int = 2) -> np.ndarray:
-    """k x k receivers on each of the six planes `inset` nodes inside the
-    layer (one plane per face), over the interior extent of that plane."""
-    lo, hi = L + inset, n - 1 - L - inset
-    span = np.round(np.linspace(L + inset, n - 1 - L - inset, k)).astype(np.int32)
-    a, b = np.meshgrid(span, span, indexing="ij")
-    a, b = a.ravel(), b.ravel()
-    out = []
-    for plane in (lo, hi):
-        out.append(np.stack([np.full_like(a, plane), a, b], 1))   # z faces
-        out.append(np.stack([a, np.full_like(a, plane), b], 1))   # y faces
-        out.append(np.stack([a, b, np.full_like(a, plane)], 1))   # x faces
-    return np.concatenate(out).astype(np.int32)
-
-
-def reflection_task(n=96, L=6, nshots=8, seed=0, nt=220, f0=15.0, c=2000.0, h=10.0, margin=40,
-                    ref_cells=20, device="cuda"):
+def reflection_task(n=96, L=6, nshots=8, seed=3, freqs=(5.0, 30.0), nfreq=4, angles=(0.0, 80.0), c=2000.0,
+                    h=10.0, margin=48, ref_cells=20, nt=None, device="cuda"):
     """Training and evaluation data of the learned layer, generated by the
-    solver itself: point sources at seeded interior positions (so that the
-    waves meet the faces at angles from normal to grazing), receivers on
-    planes just inside the layer on all six faces, and reference traces from
-    the same interior embedded in a grid `margin` nodes larger per side (its
-    own 20-cell polynomial layer far away), where nothing returns to the
-    receivers within the window.  The misfit against the reference is the
-    energy reflected by the thin layer."""
+    solver itself on an n^3 homogeneous grid:
+      - nfreq frequency groups, f0 drawn (seeded, one per equal sub-range)
+        from `freqs`; each group has its own Ricker wavelet and window
+        nt = (2.4 / f0 + 0.3 s) / dt unless given;
+      - per group, training and held-out shots whose sources meet a seeded
+        face at seeded incidence angles in `angles` (synth.angled_sources);
+      - receivers on the six planes 2 nodes inside the layer
+        (synth.face_receivers, 5 x 5 per face);
+      - reference traces from the same interior embedded in a grid `margin`
+        nodes larger per side (its own ref_cells-cell polynomial layer far
+        away), where nothing returns to the receivers within the window.
+    The misfit against the reference is the energy the thin layer reflects."""
     from .fdtd import Fdtd
-    from .synth import ricker
     dt = 0.5 * h / c
-    rng = np.random.default_rng(seed)
-    lo, hi = L + 6, n - L - 6
-    src = {k: rng.integers(lo, hi, size=(nshots, 3)).astype(np.int32) for k in ("train", "eval")}
-    rec = _face_receivers(n, L, 5)
-    wav = np.tile(ricker(nt, dt, f0)[None, :], (nshots, 1)).astype(np.float32)
+    f0s = frequency_groups(freqs, nfreq, seed)
+    rec = face_receivers(n, L, 5)
+    groups = []
+    for k, f0 in enumerate(f0s):
+        ntk = int(nt) if nt else int(math.ceil((2.4 / f0 + 0.3) / dt))
+        src, th = {}, {}
+        for j, which in enumerate(("train", "eval")):
+            src[which], th[which], _ = angled_sources(n, L, nshots, seed * 1000 + 2 * k + j, angles)
+        wav = np.tile(ricker(ntk, dt, f0)[None, :], (nshots, 1)).astype(np.float32)
+        groups.append(dict(f0=f0, nt=ntk, src=src, angles=th, wav=wav))
+    nt_max = max(g["nt"] for g in groups)
     nb = n + 2 * margin
-    big = Fdtd((nb,) * 3, h, dt, nshots=nshots, cpml_cells=ref_cells, nt_max=nt, nrec_max=len(rec), device=device)
+    big = Fdtd((nb,) * 3, h, dt, nshots=nshots, cpml_cells=ref_cells, nt_max=nt_max, nrec_max=len(rec), device=device)
     big.set_model(torch.full((nb,) * 3, c, device=device))
     big.set_cpml(R=1e-8, c_ref=c)
     big.record(rec + margin)
-    refs = {}
-    for k in ("train", "eval"):
-        big.reset()
-        big.inject(src[k] + margin, torch.from_numpy(wav).to(device))
-        big.step(nt)
-        refs[k] = big.traces.clone()
+    zeros = None
+    for g in groups:
+        g["ref"], g["ref_energy"] = {}, {}
+        for which in ("train", "eval"):
+            big.reset()
+            big.inject(g["src"][which] + margin, torch.from_numpy(g["wav"]).to(device))
+            big.step(g["nt"])
+            big.sync()
+            ref = torch.zeros_like(big.traces)
+            ref[:, :g["nt"]] = big.traces[:, :g["nt"]]
+            if zeros is None:
+                zeros = torch.zeros_like(ref)
+            g["ref"][which] = ref
+            g["ref_energy"][which] = misfit_flat(ref, zeros)
     big.close()
-    return dict(n=n, L=L, nshots=nshots, nt=nt, f0=f0, c=c, h=h, dt=dt, src=src, rec=rec, wav=wav, ref=refs,
-                device=device)
+    return dict(n=n, L=L, nshots=nshots, c=c, h=h, dt=dt, rec=rec, groups=groups, nt_max=nt_max, device=device,
+                freqs=tuple(freqs), angles=tuple(angles))
 
 
-def _reflection(sim, task, which):
+def _reflection(sim, task, g, which):
+    """||traces - ref|| / ||ref|| of one group's shots (library misfits)."""
     sim.reset()
-    sim.inject(task["src"][which], torch.from_numpy(task["wav"]).to(task["device"]))
-    sim.step(task["nt"])
-    ref = task["ref"][which]
-    num = float(((sim.traces - ref) ** 2).sum())
-    den = float((ref ** 2).sum())
-    return math.sqrt(num / den)
+    sim.inject(g["src"][which], torch.from_numpy(g["wav"]).to(task["device"]))
+    sim.step(g["nt"])
+    J = sim.misfit(g["ref"][which], nt=g["nt"])
+    return math.sqrt(J / g["ref_energy"][which])
 
 
-def train_learned_cpml(task, iters=60, lr=5e-3, seed=0, checkpoint_every=25, fit_iters=400):
+def train_learned_cpml(task, iters=48, lr=5e-3, seed=0, checkpoint_every=25, fit_iters=400):
     """Fit the network to the polynomial grading of the same thickness (the
-    fallback), then train it through the adjoint on the reflection task.
-    Returns reflection ratios ||traces - ref|| / ||ref|| on held-out shots for
-    the polynomial and the learned layer, the training misfits, and the
-    learned (sigma, kappa, alpha)."""
+    fallback), then train it through the adjoint on the reflection task,
+    cycling through the frequency groups (the network's frequency input
+    changes from step to step); each group's misfit is weighted by the
+    inverse of its reference energy, so every group counts as its squared
+    reflection ratio.  Returns per group the reflection ratios ||traces -
+    ref|| / ||ref|| on held-out shots for the polynomial and the learned
+    layer, the training misfits and the model."""
     from .fdtd import Fdtd
-    n, L, nt, dev = task["n"], task["L"], task["nt"], task["device"]
+    n, L, dev = task["n"], task["L"], task["device"]
     shape = (n,) * 3
-    sim = Fdtd(shape, task["h"], task["dt"], nshots=task["nshots"], cpml_cells=L, nt_max=nt,
+    sim = Fdtd(shape, task["h"], task["dt"], nshots=task["nshots"], cpml_cells=L, nt_max=task["nt_max"],
                nrec_max=len(task["rec"]), checkpoint_every=checkpoint_every, cpml_grad=True, device=dev)
     sim.set_model(torch.full(shape, task["c"], device=dev))
     sim.record(task["rec"])
     # polynomial grading of the same thickness (paper Tab. 2 parameters)
     sim.set_cpml(R=1e-8, kappa_max=5.0, alpha_frac=0.05, q=3, c_ref=task["c"])
-    poly_eval = _reflection(sim, task, "eval")
-    model = LearnedCPML(L, task["h"], task["dt"], task["c"], task["f0"], seed=seed, device=dev)
-    fit_err = model.fit_profile(roden_gedney_ska(L, task["h"], task["c"]), iters=fit_iters)
-    sim.reset()
-    sim.inject(task["src"]["train"], torch.from_numpy(task["wav"]).to(dev))
+    groups = task["groups"]
+    poly = [_reflection(sim, task, g, "eval") for g in groups]
+    model = LearnedCPML(L, task["h"], task["dt"], task["c"], groups[0]["f0"], seed=seed, device=dev)
+    fit_err = model.fit_profile(polynomial_ska(L, task["h"], task["c"]), iters=fit_iters)
     Js = []
-    for _ in range(iters):
-        Js.append(model.train_step(sim, task["ref"]["train"], nt, lr=lr))
-    ska, _ = model.ska()
-    sim.set_cpml_ska(ska)
-    learned_eval = _reflection(sim, task, "eval")
+    for it in range(iters):
+        g = groups[it % len(groups)]
+        model.set_frequency(g["f0"])
+        sim.inject(g["src"]["train"], torch.from_numpy(g["wav"]).to(dev))
+        Js.append(model.train_step(sim, g["ref"]["train"], g["nt"], lr=lr, weight=1.0 / g["ref_energy"]["train"]))
+    learned = []
+    for g in groups:
+        model.set_frequency(g["f0"])
+        ska, _ = model.ska()
+        sim.set_cpml_ska(ska)
+        learned.append(_reflection(sim, task, g, "eval"))
     sim.close()
-    return dict(poly_eval=poly_eval, learned_eval=learned_eval, J_first=Js[0], J_last=Js[-1], J=Js,
-                fit_err=fit_err, ska=ska.cpu().numpy(), model=model)
+    ng = len(groups)
+    return dict(f0=[g["f0"] for g in groups], poly_eval=poly, learned_eval=learned,
+                J_first=float(np.mean(Js[:ng])), J_last=float(np.mean(Js[-ng:])), J=Js, fit_err=fit_err,
+                model=model)
 
 
-__all__ = ["LearnedCPML", "Network", "features", "roden_gedney_ska", "init_params", "NPARAM", "reflection_task",
-           "train_learned_cpml"]
+__all__ = ["LearnedCPML", "Network", "features", "polynomial_ska", "NPARAM", "reflection_task", "train_learned_cpml",
+           "misfit_flat"]

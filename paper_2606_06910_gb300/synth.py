@@ -104,6 +104,78 @@ def receiver_grid(shape, L, nry: int, nrx: int, z: int):
     return np.stack([np.full(yy.size, z, np.int32), yy.ravel(), xx.ravel()], axis=1)
 
 
+def face_receivers(n: int, L: int, k: int, inset: int = 2) -> np.ndarray:
+    """k x k receivers on each of the six planes `inset` nodes inside the
+    inner edge of an L-cell layer on a cube of n nodes, over the interior
+    extent of that plane.  Returns int32 [6 k^2, 3] of (z, y, x)."""
+    lo, hi = L + inset, n - 1 - L - inset
+    span = np.round(np.linspace(lo, hi, k)).astype(np.int32)
+    a, b = np.meshgrid(span, span, indexing="ij")
+    a, b = a.ravel(), b.ravel()
+    out = []
+    for plane in (lo, hi):
+        out.append(np.stack([np.full_like(a, plane), a, b], 1))   # z faces
+        out.append(np.stack([a, np.full_like(a, plane), b], 1))   # y faces
+        out.append(np.stack([a, b, np.full_like(a, plane)], 1))   # x faces
+    return np.concatenate(out).astype(np.int32)
+
+
+def angled_sources(n: int, L: int, nshots: int, seed: int, angles=(0.0, 80.0), inset: int = 2,
+                   d_max: int = 40, clearance: int = 6):
+    """Point sources for CPML reflection tasks on a cube of n nodes with an
+    L-cell layer: shot s draws a face, an incidence angle theta in `angles`
+    (degrees) and an azimuth, and sits at normal distance d from the face's
+    receiver plane (face_receivers) with lateral offset d tan(theta) from the
+    plane's centre, so that its wave meets the middle of that face at theta;
+    d is as large as fits (at most d_max) with the source at least
+    `clearance` nodes clear of the layer.  Returns (int32 [nshots, 3] of
+    (z, y, x), the angles in degrees, the faces in FACE_ORDER order)."""
+    rng = np.random.default_rng(seed)
+    lo_src, hi_src = L + clearance, n - 1 - L - clearance
+    plane = {0: L + inset, 1: n - 1 - L - inset}
+    centre = (n - 1) / 2.0
+    half = centre - lo_src
+    out, th, fc = [], [], []
+    for _ in range(nshots):
+        face = int(rng.integers(6))
+        theta = float(rng.uniform(*angles))
+        phi = float(rng.uniform(0.0, 2.0 * math.pi))
+        t = math.tan(math.radians(theta))
+        d = float(d_max) if t * d_max <= half else half / t
+        d = max(d, float(lo_src - plane[0]) + 1.0)
+        axis, side = face // 2, face % 2
+        normal = plane[side] + (d if side == 0 else -d)
+        lat = (centre + d * t * math.cos(phi), centre + d * t * math.sin(phi))
+        pos = [0.0, 0.0, 0.0]                   # (x, y, z)
+        pos[axis] = normal
+        others = [a for a in range(3) if a != axis]
+        pos[others[0]], pos[others[1]] = lat
+        zyx = [int(np.clip(round(pos[2 - i]), lo_src, hi_src)) for i in range(3)]
+        out.append(zyx)
+        th.append(theta)
+        fc.append(FACE_ORDER[face])
+    return np.array(out, dtype=np.int32), np.array(th), fc
+
+
+def frequency_groups(freqs, nfreq: int, seed: int):
+    """nfreq dominant frequencies, one drawn uniformly (seeded) from each of
+    nfreq equal sub-ranges of freqs = (f_lo, f_hi)."""
+    rng = np.random.default_rng(seed)
+    edges = np.linspace(freqs[0], freqs[1], nfreq + 1)
+    return [float(rng.uniform(edges[k], edges[k + 1])) for k in range(nfreq)]
+
+
+def mlp_init_params(seed: int, scale1=0.5, scale2=0.2, scale3=0.1) -> np.ndarray:
+    """Seeded initial weights of the 4 -> 64 -> 64 -> 3 network (normal,
+    fixed scales) and zero biases, flattened as W1, b1, W2, b2, W3, b3;
+    float64."""
+    rng = np.random.default_rng(seed)
+    W1 = scale1 * rng.standard_normal((64, 4))
+    W2 = scale2 * rng.standard_normal((64, 64))
+    W3 = scale3 * rng.standard_normal((3, 64))
+    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), W3.ravel(), np.zeros(3)])
+
+
 def slab_mask(n: int, lo: int, hi: int):
     m = np.zeros(n, dtype=bool)
     m[:lo] = True

@@ -137,3 +137,21 @@ def test_noalloc_limit_matches_header():
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "fdtd.h")).read()
     m = re.search(r"#define FDTD_NOALLOC_MISFIT_MAX (\d+)LL", hdr)
     assert m and int(m.group(1)) == _lib.NOALLOC_MISFIT_MAX
+
+
+@pytest.mark.parametrize("L,q,R,kmax,af", [(6, 3, 1e-8, 5.0, 0.05), (20, 2, 1e-5, 1.0, 0.0), (1, 3, 1e-3, 3.0, 0.1)])
+def test_cpml_grading_matches_oracle_profile(lib, L, q, R, kmax, af):
+    # the library's per-cell (sigma, kappa, alpha) against the oracle's low
+    # face, node j = cell j (host computation, no GPU)
+    from oracle import oracle as O
+    h, c = 10.0, 2000.0
+    out = (ctypes.c_double * (3 * L))()
+    assert lib.fdtd_cpml_grading(L, h, c, R, kmax, af, q, out) == _lib.OK
+    ska = [[out[3 * j + k] for k in range(3)] for j in range(L)]
+    prof = O.axis_profile(3 * L + 4, L, L, h, 1e-3, c, R, q, kmax, af)
+    for j in range(L):
+        for k, name in enumerate(("sigma", "kappa", "alpha")):
+            assert abs(ska[j][k] - prof[name][j]) <= 1e-12 * max(1.0, abs(prof[name][j])), (j, name)
+    assert lib.fdtd_cpml_grading(0, h, c, R, kmax, af, q, out) == _lib.EINVAL
+    assert lib.fdtd_cpml_grading(L, h, c, 2.0, kmax, af, q, out) == _lib.EINVAL
+    assert lib.fdtd_cpml_grading(L, h, c, R, kmax, af, q, None) == _lib.EINVAL

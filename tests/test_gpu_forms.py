@@ -1,7 +1,5 @@
 """The precision form (FP16 / BF16 storage, FP32 arithmetic) and the learned
 CPML form, through the C ABI, against the FP64 oracle."""
-import math
-
 import numpy as np
 import pytest
 
@@ -23,46 +21,107 @@ def _Fdtd():
 # ---------------------------------------------------------------------------
 # precision form: 128^3 accuracy instance of the 1024^3 layered workload
 # ---------------------------------------------------------------------------
-@pytest.fixture(scope="module")
-def oracle128():
-    w = synth.preset("layered128")
+CHECKPOINTS = (250, 375, 500)
+
+
+def _oracle_run(w, store=None, sp=1.0, sv=1.0):
     vel = w.velocity()
     g = O.Grid(vel.astype(np.float64) ** 2, w.h, w.dt,
-               O.make_profiles(w.shape, w.cpml_cells, w.h, w.dt, w.vmax, R=w.R))
+               O.make_profiles(w.shape, w.cpml_cells, w.h, w.dt, w.vmax, R=w.R),
+               store=store, scale_p=sp, scale_v=sv)
     st = O.State(w.shape)
     src = tuple(w.sources()[0])
     wav = w.wavelet()[0].astype(np.float64)
     rec = synth.receiver_grid(w.shape, w.cpml_cells, 6, 6, w.cpml_cells[4])
-    tr1 = O.run(g, st, 250, 0, src, wav, rec)
-    p250 = st["p"].copy()
-    tr2 = O.run(g, st, w.nt - 250, 250, src, wav, rec)
-    return dict(w=w, vel=vel, rec=rec, p250=p250, p500=st["p"].copy(), traces=np.concatenate([tr1, tr2]))
+    out, t, trs = {}, 0, []
+    for c in CHECKPOINTS:
+        trs.append(O.run(g, st, c - t, t, src, wav, rec))
+        t = c
+        out[c] = st["p"].copy()
+    out["traces"] = np.concatenate(trs)
+    return out
 
 
-@pytest.mark.parametrize("storage,budget,budget_end", [("f32", 1e-4, 1e-4), ("f16", 2e-2, 3e-2),
-                                                       ("bf16", 5e-2, 2.5e-1)])
-def test_storage_accuracy_against_oracle(oracle128, storage, budget, budget_end):
-    """Relative L2 of the pressure against the FP64 oracle after 250 steps and
-    of the receiver traces over the run (budget 2e-2 for FP16; BF16's 8-bit
-    mantissa is reported against a looser bound), and of the pressure after
-    the last (500th) step, when most of the wave has left through the layer
-    and the field is the small residual (FP16 measured 2.06e-2 there)."""
+@pytest.fixture(scope="module")
+def oracle128():
+    w = synth.preset("layered128")
+    rec = synth.receiver_grid(w.shape, w.cpml_cells, 6, 6, w.cpml_cells[4])
+    return dict(w=w, vel=w.velocity(), rec=rec, ref=_oracle_run(w))
+
+
+def _gpu_errors(o, storage):
+    """Relative L2 of the GPU's pressure after steps 250, 375, 500 and of its
+    traces against the oracle run `o["ref"]`."""
     Fdtd = _Fdtd()
-    o = oracle128
     w = o["w"]
     sim = Fdtd(w.shape, w.h, w.dt, cpml_cells=w.cpml_cells, storage=storage, nt_max=w.nt, nrec_max=len(o["rec"]))
     sim.set_model(torch.from_numpy(o["vel"]).cuda())
     sim.set_cpml(R=w.R, c_ref=w.vmax)
     sim.inject(w.sources(), torch.from_numpy(w.wavelet()).cuda())
     traces = sim.record(o["rec"])
-    sim.step(250)
-    e250 = rel_errors(sim.get("p").cpu().numpy(), o["p250"])
-    sim.step(w.nt - 250)
+    e, t = {}, 0
+    for c in CHECKPOINTS:
+        sim.step(c - t)
+        t = c
+        e[c] = rel_errors(sim.get("p").cpu().numpy(), o["ref"][c])[0]
     sim.sync()
-    e500 = rel_errors(sim.get("p").cpu().numpy(), o["p500"])
-    et = rel_errors(traces[0].cpu().numpy(), o["traces"])
-    print(f"\n[precision] {storage}: rel L2 p@250 {e250[0]:.3e}, p@500 {e500[0]:.3e}, traces {et[0]:.3e}")
-    assert e250[0] <= budget and et[0] <= budget and e500[0] <= budget_end
+    e["traces"] = rel_errors(traces[0].cpu().numpy(), o["ref"]["traces"])[0]
+    print(f"\n[precision] {storage}: " + ", ".join(f"{k}: {v:.3e}" for k, v in e.items()))
+    return e
+
+
+def test_f32_storage_within_its_tolerance(oracle128):
+    e = _gpu_errors(oracle128, "f32")
+    assert all(v <= 1e-4 for v in e.values()), e
+
+
+def test_f16_storage_within_budget_while_the_wave_is_in_the_grid(oracle128):
+    """The benchmark spec's 2e-2 relative L2 budget, asserted as stated, for the
+    pressure after 250 and 375 steps and for the traces of the whole run."""
+    e = _gpu_errors(oracle128, "f16")
+    assert e[250] <= 2e-2 and e[375] <= 2e-2 and e["traces"] <= 2e-2, e
+
+
+@pytest.fixture(scope="module")
+def rounded128(oracle128):
+    """The oracle with the 16-bit storage form's rounding (FP64 arithmetic,
+    every stored field rounded to FP16 / BF16 as the form stores it): the
+    error that the storage format alone causes."""
+    o = oracle128
+    w = o["w"]
+    out = {}
+    for st, sp in (("f16", 1024.0), ("bf16", 1.0)):
+        r = _oracle_run(w, st, sp, float(w.vmax))
+        out[st] = {c: rel_errors(r[c], o["ref"][c])[0] for c in CHECKPOINTS}
+        out[st]["traces"] = rel_errors(r["traces"], o["ref"]["traces"])[0]
+    return out
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_16bit_error_is_the_storage_rounding(oracle128, rounded128, storage):
+    """Where the 16-bit forms miss the 2e-2 budget (FP16: the pressure after
+    500 steps, when the wave has mostly left and the field is the small
+    residual; BF16: everywhere), the miss is the storage format's own: the
+    GPU's error is within 25 % of the error of FP64 arithmetic with the same
+    storage rounding.  The noise realisations differ (one rounding decided
+    differently spreads), so the sizes are compared, not the fields."""
+    e = _gpu_errors(oracle128, storage)
+    floor = rounded128[storage]
+    for k in e:
+        assert abs(e[k] - floor[k]) <= 0.25 * floor[k], (k, e[k], floor[k])
+
+
+@pytest.mark.xfail(reason="over budget: FP16 storage gives 2.06e-2 after 500 steps (2e-2 budget); the storage "
+                          "rounding alone gives 2.1e-2 (test_16bit_error_is_the_storage_rounding)", strict=False)
+def test_f16_storage_within_budget_after_absorption(oracle128):
+    assert _gpu_errors(oracle128, "f16")[500] <= 2e-2
+
+
+@pytest.mark.xfail(reason="over budget: BF16's 8-bit significand gives 2.2e-2 to 1.7e-1 (2e-2 budget), as the "
+                          "storage rounding alone does (test_16bit_error_is_the_storage_rounding)", strict=False)
+def test_bf16_storage_within_budget(oracle128):
+    e = _gpu_errors(oracle128, "bf16")
+    assert all(v <= 2e-2 for v in e.values()), e
 
 
 # ---------------------------------------------------------------------------
@@ -147,16 +206,18 @@ def test_learned_gradient_matches_oracle():
 
 def test_learned_layer_beats_polynomial_layer_of_same_thickness():
     """Train the 6-cell learned grading on reflections the solver generates
-    (64^3 homogeneous, shots at seeded positions so waves meet the faces at
-    many angles), then compare reflections on held-out shots: the learned
-    6-cell layer reflects less than the 6-cell polynomial grading."""
+    (64^3 homogeneous; two frequency groups drawn from 12-30 Hz; shots that
+    meet seeded faces at seeded angles 0-80 degrees), then compare reflections
+    on held-out shots of each group: the learned 6-cell layer reflects less
+    than the 6-cell polynomial grading at every frequency."""
     from paper_2606_06910_gb300.learned import reflection_task, train_learned_cpml
-    task = reflection_task(n=64, L=6, nshots=4, seed=1, nt=150, f0=15.0)
+    task = reflection_task(n=64, L=6, nshots=4, seed=1, freqs=(12.0, 30.0), nfreq=2, margin=40)
     res = train_learned_cpml(task, iters=60, lr=5e-3, seed=0)
-    print(f"\n[learned CPML] reflection: polynomial-6 {res['poly_eval']:.4e}, learned-6 {res['learned_eval']:.4e}, "
-          f"training J {res['J_first']:.3e} -> {res['J_last']:.3e}")
+    print(f"\n[learned CPML] f0 {res['f0']}: reflection polynomial-6 {res['poly_eval']}, learned-6 "
+          f"{res['learned_eval']}, training J {res['J_first']:.3e} -> {res['J_last']:.3e}")
     assert res["J_last"] < res["J_first"]
-    assert res["learned_eval"] < 0.9 * res["poly_eval"]
+    for p, l in zip(res["poly_eval"], res["learned_eval"]):
+        assert l < 0.9 * p, (l, p)
 
 
 @pytest.mark.parametrize("storage,tol", [("f16", 4e-3), ("bf16", 3e-2)])
