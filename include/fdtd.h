@@ -263,6 +263,19 @@ int fdtd_adjoint_step_n(fdtd_ctx *ctx, int n, const float *resid_dev,
 int fdtd_get_field(fdtd_ctx *ctx, int which, int shot, float *dst_dev);
 int fdtd_set_field(fdtd_ctx *ctx, int which, int shot, const float *src_dev);
 
+/* Halo exchange of the domain decomposition of Sec. 3.3: copy the stepped
+ * state -- p, v and the CPML memory variables, every shot -- over the box
+ * box = {z0, z1, y0, y1, x0, x1} of dst's grid from the nodes
+ * (z + shift[0], y + shift[1], x + shift[2]) of src's grid.  The two contexts
+ * hold parts of one grid (with the CPML on the grid's outer faces only, as in
+ * Sec. 3.3), so a memory variable psi_d is copied where both keep it (a node
+ * in the d-slabs of both).  Both must have the same storage, shots and form
+ * and the same time index (ESTATE otherwise); EINVAL if a box leaves either
+ * grid.  The copy is one kernel on dst's stream that reads src's arrays
+ * directly: src's last step must be complete or on the same stream.  The
+ * adjoint state and checkpoints are not exchanged. */
+int fdtd_exchange(fdtd_ctx *dst, const fdtd_ctx *src, const int box[6], const int shift[3]);
+
 /* Zero every field and memory variable, time index 0 (model, CPML, source and
  * receivers are kept). */
 int fdtd_reset(fdtd_ctx *ctx);

@@ -32,6 +32,7 @@ cudaError_t launch_adam(float *th, const float *g, float *m, float *v, int n, fl
                         float c1, float c2, cudaStream_t s);
 cudaError_t launch_fit_gradient(const float *out, const float *tgt, int n, float ssc, float asc, float *gout,
                                 float *loss, cudaStream_t s);
+cudaError_t launch_exchange(fdtd_ctx *dst, const fdtd_ctx *src, const int box[6], const int shift[3]);
 cudaError_t launch_adj_inject(const fdtd_ctx *c, const float *resid, int n);
 cudaError_t launch_grad_vel(const fdtd_ctx *c, float *grad_vel);
 cudaError_t adjoint_step(fdtd_ctx *c, const float *s_tape, float *const slab_tape[3], bool want_prof);
@@ -1459,6 +1460,28 @@ int fdtd_timing(fdtd_ctx *c, int kernel_class, double *ms, long long *launches)
         *ms = c->t_ms[kernel_class];
     if (launches)
         *launches = c->t_launch[kernel_class];
+    return FDTD_OK;
+}
+
+int fdtd_exchange(fdtd_ctx *dst, const fdtd_ctx *src, const int box[6], const int shift[3])
+{
+    if (!dst || !src || !box || !shift)
+        return dst ? fail(dst, FDTD_EINVAL, "NULL argument") : FDTD_EINVAL;
+    if (dst == src)
+        return fail(dst, FDTD_EINVAL, "source and destination are the same context");
+    if (dst->d.storage != src->d.storage || dst->d.nshots != src->d.nshots || dst->staggered != src->staggered)
+        return fail(dst, FDTD_EINVAL, "contexts differ in storage, shots or form");
+    if (dst->t != src->t)
+        return fail(dst, FDTD_ESTATE, "contexts are at different time indices (%d, %d)", dst->t, src->t);
+    const int nd[3] = {dst->g.nz, dst->g.ny, dst->g.nx}, ns[3] = {src->g.nz, src->g.ny, src->g.nx};
+    for (int a = 0; a < 3; ++a) {
+        const int lo = box[2 * a], hi = box[2 * a + 1];
+        if (lo > hi || lo < 0 || hi > nd[a] || lo + shift[a] < 0 || hi + shift[a] > ns[a])
+            return fail(dst, FDTD_EINVAL, "box [%d, %d) + %d outside the grids on axis %c", lo, hi, shift[a], "zyx"[a]);
+    }
+    if (box[0] == box[1] || box[2] == box[3] || box[4] == box[5])
+        return FDTD_OK;
+    CUDA_TRY(dst, launch_exchange(dst, src, box, shift));
     return FDTD_OK;
 }
 
