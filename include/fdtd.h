@@ -130,6 +130,15 @@ const char *fdtd_last_error(const fdtd_ctx *ctx);
  * collocated radius-4 leapfrog limit 2 / (sqrt(3) max_theta 2 sum_l a_l sin(l theta)) = 0.6672. */
 int fdtd_set_model(fdtd_ctx *ctx, const float *vel_dev, const float *rho_dev);
 
+/* Velocity scale of 16-bit storage: the stored velocity is scale * v (an
+ * impedance scaling that keeps the stored v of the order of p; the memory
+ * variables of the pressure update carry the same scale).  scale = 0 (the
+ * default) takes the model's maximum velocity.  Takes effect at the next
+ * fdtd_set_model; FP32 storage ignores it.  Contexts that hold parts of one
+ * grid (fdtd_exchange) must store at the same scale.  EINVAL for a negative
+ * or non-finite scale. */
+int fdtd_set_velocity_scale(fdtd_ctx *ctx, double scale);
+
 /* CPML grading of Sec. 3.2 / Tab. 2 on the cells given at create time:
  *   sigma = sigma_max rho^q, sigma_max = -(q+1) c_ref ln(R) / (2 L h),
  *   kappa = 1 + (kappa_max - 1) rho^q, alpha = alpha_frac sigma_max (1 - rho),
@@ -271,7 +280,8 @@ int fdtd_set_field(fdtd_ctx *ctx, int which, int shot, const float *src_dev);
  * Sec. 3.3), so a memory variable psi_d is copied where both keep it (a node
  * in the d-slabs of both).  Both must have the same storage, shots and form
  * and the same time index (ESTATE otherwise); EINVAL if a box leaves either
- * grid.  The copy is one kernel on dst's stream that reads src's arrays
+ * grid, or if the two store velocities at different scales (see
+ * fdtd_set_velocity_scale).  The copy is one kernel on dst's stream that reads src's arrays
  * directly: src's last step must be complete or on the same stream.  The
  * adjoint state and checkpoints are not exchanged. */
 int fdtd_exchange(fdtd_ctx *dst, const fdtd_ctx *src, const int box[6], const int shift[3]);

@@ -71,6 +71,7 @@ _SIGS = {
     "fdtd_misfit": (c_int, [c_void_p, c_void_p, c_int, c_void_p, ctypes.POINTER(c_double)]),
     "fdtd_misfit_noalloc": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_void_p,
                                     ctypes.POINTER(c_double), c_void_p]),
+    "fdtd_set_velocity_scale": (c_int, [c_void_p, c_double]),
     "fdtd_exchange": (c_int, [c_void_p, c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "fdtd_set_timing": (c_int, [c_void_p, c_int]),
     "fdtd_timing": (c_int, [c_void_p, c_int, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong)]),

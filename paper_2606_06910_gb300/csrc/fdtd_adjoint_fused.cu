@@ -24,7 +24,8 @@
 // from the slabs differentiate the staged mu plane directly.  mu and lam_v
 // are read from one set and written to the other; so are the memory
 // variables.  One pass reads mu, lam_v, kdt, the tape and dJ/dK and writes
-// mu, lam_v and dJ/dK (52 B per node, FP32), plus the slab memory variables.
+// mu, lam_v and dJ/dK (48 B per node and shot, FP32: 7 words read, 5 written),
+// plus the slab memory variables (16 B per slab node and axis).
 #include "fdtd_internal.cuh"
 
 namespace fdtd {

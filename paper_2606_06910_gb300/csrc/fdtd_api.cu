@@ -936,7 +936,7 @@ int fdtd_set_model(fdtd_ctx *c, const float *vel, const float *rho)
     c->c_max = vmax;
     if (c->d.storage != FDTD_F32) {
         // impedance scaling keeps the stored velocities O(p) in 16-bit
-        c->vscale = vmax;
+        c->vscale = c->vscale_req > 0.f ? c->vscale_req : vmax;
         CUDA_TRY(c, launch_model(c, vel, rho));
     }
     c->var_rho = rho != nullptr;
@@ -1463,6 +1463,16 @@ int fdtd_timing(fdtd_ctx *c, int kernel_class, double *ms, long long *launches)
     return FDTD_OK;
 }
 
+int fdtd_set_velocity_scale(fdtd_ctx *c, double scale)
+{
+    if (!c)
+        return FDTD_EINVAL;
+    if (!(scale >= 0.0) || !std::isfinite(scale) || scale > 3.0e38)
+        return fail(c, FDTD_EINVAL, "velocity scale must be finite and >= 0");
+    c->vscale_req = (float)scale;
+    return FDTD_OK;
+}
+
 int fdtd_exchange(fdtd_ctx *dst, const fdtd_ctx *src, const int box[6], const int shift[3])
 {
     if (!dst || !src || !box || !shift)
@@ -1473,6 +1483,9 @@ int fdtd_exchange(fdtd_ctx *dst, const fdtd_ctx *src, const int box[6], const in
         return fail(dst, FDTD_EINVAL, "contexts differ in storage, shots or form");
     if (dst->t != src->t)
         return fail(dst, FDTD_ESTATE, "contexts are at different time indices (%d, %d)", dst->t, src->t);
+    if (dst->vscale != src->vscale || dst->sscale != src->sscale)
+        return fail(dst, FDTD_EINVAL, "contexts store velocities at different scales (%g, %g): use "
+                                      "fdtd_set_velocity_scale", (double)dst->vscale, (double)src->vscale);
     const int nd[3] = {dst->g.nz, dst->g.ny, dst->g.nx}, ns[3] = {src->g.nz, src->g.ny, src->g.nx};
     for (int a = 0; a < 3; ++a) {
         const int lo = box[2 * a], hi = box[2 * a + 1];

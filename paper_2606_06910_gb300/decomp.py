@@ -126,8 +126,13 @@ class Decomposition:
         return vol[z0:z1, y0:y1, x0:x1].contiguous()
 
     def set_model(self, vel: torch.Tensor):
+        """The whole grid's model, each part given its box.  With 16-bit
+        storage every part stores velocities at the whole model's maximum
+        velocity (the scale one grid would use), so that exchanged values
+        need no conversion."""
         self.c_max = float(vel.max())
         for sub in self.subs:
+            sub["sim"].set_velocity_scale(self.c_max)
             sub["sim"].set_model(self._crop(vel, sub))
 
     def set_cpml(self, R=1e-8, kappa_max=5.0, alpha_frac=0.05, q=3, c_ref=None):

@@ -200,6 +200,11 @@ class Fdtd:
     def sync(self):
         self._check(self.lib.fdtd_sync(self.ctx))
 
+    def set_velocity_scale(self, scale: float):
+        """Stored velocity = scale * v with 16-bit storage (0: the model's
+        maximum velocity); takes effect at the next set_model."""
+        self._check(self.lib.fdtd_set_velocity_scale(self.ctx, float(scale)))
+
     # -- kernel timing (CUDA events around each launch, in the library) -------
     def set_timing(self, on: bool = True):
         self._check(self.lib.fdtd_set_timing(self.ctx, 1 if on else 0))

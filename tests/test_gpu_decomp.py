@@ -109,3 +109,13 @@ def test_exchange_validates_its_arguments():
     a.step(1)
     assert lib.fdtd_exchange(a.ctx, b.ctx, box, ok) == _lib.ESTATE
     a.sync()
+    # 16-bit parts must store velocities at one scale
+    c = Fdtd((20, 20, 20), 10.0, 1e-3, nt_max=4, storage="f16")
+    d = Fdtd((20, 20, 20), 10.0, 1e-3, nt_max=4, storage="f16")
+    c.set_model(torch.full((20, 20, 20), 2000.0, device="cuda"))
+    d.set_model(torch.full((20, 20, 20), 2500.0, device="cuda"))
+    assert lib.fdtd_exchange(c.ctx, d.ctx, box, ok) == _lib.EINVAL
+    c.set_velocity_scale(2500.0)
+    c.set_model(torch.full((20, 20, 20), 2000.0, device="cuda"))
+    assert lib.fdtd_exchange(c.ctx, d.ctx, box, ok) == _lib.OK
+    c.sync()
