@@ -293,6 +293,12 @@ int fdtd_reset(fdtd_ctx *ctx);
 /* Current time index (steps taken since create/reset). */
 int fdtd_time(const fdtd_ctx *ctx, int *t);
 
+/* Set the time index (resume: with the fields restored by fdtd_set_field, a
+ * run continues from step t, sampling wavelets and recording traces at t and
+ * after).  EINVAL if t < 0; EUNSUPPORTED for a context with checkpoints,
+ * whose adjoint replays from step 0. */
+int fdtd_set_time(fdtd_ctx *ctx, int t);
+
 /* Wait for the stream and report device-side errors (ETIMEOUT, EDIVERGED). */
 int fdtd_sync(fdtd_ctx *ctx);
 

@@ -1412,6 +1412,18 @@ int fdtd_time(const fdtd_ctx *c, int *t)
     return FDTD_OK;
 }
 
+int fdtd_set_time(fdtd_ctx *c, int t)
+{
+    if (!c)
+        return FDTD_EINVAL;
+    if (t < 0)
+        return fail(c, FDTD_EINVAL, "time index must be >= 0");
+    if (c->d.checkpoint_every > 0)
+        return fail(c, FDTD_EUNSUPPORTED, "the time index of a context with checkpoints starts at 0");
+    c->t = t;
+    return FDTD_OK;
+}
+
 int fdtd_sync(fdtd_ctx *c)
 {
     if (!c)

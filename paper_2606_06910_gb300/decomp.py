@@ -98,7 +98,7 @@ class Decomposition:
     along (x, y, z), exchanging ghosts of depth 8 s every s steps."""
 
     def __init__(self, shape, h, dt, parts=(1, 2, 2), s=1, *, nshots=1, cpml_cells=0, storage="f32", nt_max=1,
-                 nrec_max=0, device=None, stream=None):
+                 nrec_max=0, cpml_local=False, device=None, stream=None):
         self.shape = tuple(int(v) for v in shape)
         self.parts = tuple(int(p) for p in parts)
         self.s = int(s)
@@ -114,7 +114,8 @@ class Decomposition:
         for part in geo:
             lshape = tuple(hi - lo for lo, hi in part["loc"])
             sim = Fdtd(lshape, h, dt, nshots=self.nshots, cpml_cells=part["cells"], storage=storage,
-                       nt_max=self.nt_max, nrec_max=nrec_max, device=self.device, stream=self.stream)
+                       nt_max=self.nt_max, nrec_max=nrec_max, cpml_local=cpml_local, device=self.device,
+                       stream=self.stream)
             self.subs.append(dict(sim=sim, own=part["own"], loc=part["loc"], rec_cols=None))
         self.links = [(i, j, (ctypes.c_int * 6)(*box), (ctypes.c_int * 3)(*shift)) for i, j, box, shift in links]
         self.traces = None
@@ -125,15 +126,26 @@ class Decomposition:
         (z0, z1), (y0, y1), (x0, x1) = sub["loc"]
         return vol[z0:z1, y0:y1, x0:x1].contiguous()
 
-    def set_model(self, vel: torch.Tensor):
-        """The whole grid's model, each part given its box.  With 16-bit
-        storage every part stores velocities at the whole model's maximum
-        velocity (the scale one grid would use), so that exchanged values
-        need no conversion."""
+    def set_model(self, vel: torch.Tensor, rho: torch.Tensor | None = None):
+        """The whole grid's model (and density), each part given its box.
+        With 16-bit storage every part stores velocities at the whole model's
+        maximum velocity (the scale one grid would use), so that exchanged
+        values need no conversion."""
         self.c_max = float(vel.max())
         for sub in self.subs:
             sub["sim"].set_velocity_scale(self.c_max)
-            sub["sim"].set_model(self._crop(vel, sub))
+            sub["sim"].set_model(self._crop(vel, sub), None if rho is None else self._crop(rho, sub))
+
+    def set_staggered(self, on: bool = True):
+        for sub in self.subs:
+            sub["sim"].set_staggered(on)
+
+    def set_cpml_local(self, vel: torch.Tensor, R=1e-8, kappa_max=5.0, alpha_frac=0.05, q=3):
+        """The local-velocity grading: every slab node's coefficients come
+        from its own velocity and its face's layer, so each part computes
+        them from its box of the model."""
+        for sub in self.subs:
+            sub["sim"].set_cpml_local(self._crop(vel, sub), R=R, kappa_max=kappa_max, alpha_frac=alpha_frac, q=q)
 
     def set_cpml(self, R=1e-8, kappa_max=5.0, alpha_frac=0.05, q=3, c_ref=None):
         """The grading of the whole grid: one reference velocity (the whole

@@ -200,6 +200,10 @@ class Fdtd:
     def sync(self):
         self._check(self.lib.fdtd_sync(self.ctx))
 
+    def set_time(self, t: int):
+        """Time index to continue from (resume after set() of every field)."""
+        self._check(self.lib.fdtd_set_time(self.ctx, int(t)))
+
     def set_velocity_scale(self, scale: float):
         """Stored velocity = scale * v with 16-bit storage (0: the model's
         maximum velocity); takes effect at the next set_model."""

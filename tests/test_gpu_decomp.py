@@ -94,6 +94,43 @@ def test_decomposed_run_equals_single_grid_fp16():
     assert torch.equal(tr, tr_ref)
 
 
+@pytest.mark.parametrize("form", ["density", "staggered", "local"])
+def test_decomposed_forms_equal_single_grid(form):
+    # the step's forms keep their per-node tables in each part's box: the
+    # density's dt / rho, the staggered half-node profiles, the local grading
+    from paper_2606_06910_gb300.decomp import Decomposition
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    c = _case()
+    dt = 0.4 * c["h"] / float(c["vel"].max()) if form == "staggered" else c["dt"]
+    vel = torch.from_numpy(c["vel"]).cuda()
+    rho = (vel / 1500.0) ** 0.25 if form == "density" else None
+    outs = []
+    for kind in ("single", "parts"):
+        if kind == "single":
+            sim = Fdtd(SHAPE, c["h"], dt, nshots=2, cpml_cells=CELLS, nt_max=c["nsteps"], nrec_max=len(c["rec"]),
+                       cpml_local=form == "local")
+        else:
+            sim = Decomposition(SHAPE, c["h"], dt, parts=(1, 2, 2), s=2, nshots=2, cpml_cells=CELLS,
+                                nt_max=c["nsteps"], nrec_max=len(c["rec"]), cpml_local=form == "local")
+        if form == "staggered":
+            sim.set_staggered(True)
+        sim.set_model(vel, rho)
+        if form == "local":
+            sim.set_cpml_local(vel, R=1e-6)
+        else:
+            sim.set_cpml(R=1e-6, c_ref=float(c["vel"].max()))
+        sim.inject(c["src"], torch.from_numpy(c["wav"]).cuda())
+        tr = sim.record(c["rec"])
+        sim.step(c["nsteps"])
+        sim.sync()
+        outs.append(({(k, s): sim.get(k, s).clone() for k in FIELDS for s in range(2)}, tr.clone()))
+        sim.close()
+    (ref, tr_ref), (out, tr) = outs
+    for key in ref:
+        assert torch.equal(out[key], ref[key]), (form, key)
+    assert torch.equal(tr, tr_ref)
+
+
 def test_exchange_validates_its_arguments():
     from paper_2606_06910_gb300.fdtd import Fdtd
     a = Fdtd((20, 20, 20), 10.0, 1e-3, nt_max=4)
