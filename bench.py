@@ -55,7 +55,7 @@ def parse():
                     help="form of the main line's step (profiling runs of the forms; FP32): the staggered grid "
                          "at CFL 0.4, the local-velocity CPML grading, or the density (c/1500)^(1/4)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--forms", default="f16,bf16,cpml_overhead,adjoint,learned,tblock,density,aniso2d,staggered,local_cpml",
+    ap.add_argument("--forms", default="f16,bf16,cpml_overhead,adjoint,learned,tblock,decomp,density,aniso2d,staggered,local_cpml",
                     help="comma list of forms measured after the main line ('' for none)")
     return ap.parse_args()
 
@@ -407,6 +407,63 @@ def form_cpml_overhead(dev, nsteps=96, warm=8):
             "overhead": round((t1 - t0) / t0, 4),
             "byte_floor": round((b1 - b0) / b0, 4),
             "target": 0.03}
+
+
+def form_decomp(dev, nsteps=48, warm=8):
+    """The paper's pencil-yz decomposition (Sec. 3.3) on one GPU: the 512^3
+    layered workload split into 1 x 2 x 2 parts with ghosts of depth 8 s,
+    exchanged every s steps (s = 1, 2, 4), against the undivided grid.
+    Reports ms per step, the exchange kernels' share (CUDA events around
+    the exchanges) and the redundant ghost work, and whether the assembled
+    pressure equals the undivided grid's bit for bit."""
+    import torch
+    from paper_2606_06910_gb300 import synth
+    from paper_2606_06910_gb300.decomp import Decomposition
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    w = synth.preset("layered512")
+    vel = torch.from_numpy(w.velocity()).to(dev)
+    npts = float(np.prod(w.shape))
+    out = {}
+    sim = Fdtd(w.shape, w.h, w.dt, cpml_cells=w.cpml_cells, nt_max=w.nt, device=dev)
+    sim.set_model(vel)
+    sim.set_cpml(R=w.R, c_ref=w.vmax)
+    sim.inject(w.sources(), torch.from_numpy(w.wavelet()).to(dev))
+    sim.step(warm)
+    secs = _timed(sim.stream, lambda: sim.step(nsteps))
+    p_ref = sim.get("p").clone()
+    out["single"] = {"value": round(npts * nsteps / secs / 1e6, 1), "ms_per_step": round(secs / nsteps * 1e3, 4)}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    for s in (1, 2, 4):
+        dec = Decomposition(w.shape, w.h, w.dt, parts=(1, 2, 2), s=s, cpml_cells=w.cpml_cells, nt_max=w.nt, device=dev)
+        dec.set_model(vel)
+        dec.set_cpml(R=w.R, c_ref=w.vmax)
+        dec.inject(w.sources(), torch.from_numpy(w.wavelet()).to(dev))
+        dec.step(warm)
+        dec.sync()
+        ex = []
+        orig = dec.exchange
+
+        def timed_exchange():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(dec.stream)
+            orig()
+            e1.record(dec.stream)
+            ex.append((e0, e1))
+        dec.exchange = timed_exchange
+        secs = _timed(dec.stream, lambda: dec.step(nsteps))
+        ex_s = sum(a.elapsed_time(b) for a, b in ex) * 1e-3
+        local = sum(float(np.prod([hi - lo for lo, hi in sub["loc"]])) for sub in dec.subs)
+        out[f"s{s}"] = {"value": round(npts * nsteps / secs / 1e6, 1), "ms_per_step": round(secs / nsteps * 1e3, 4),
+                        "exchange_ms_per_step": round(ex_s / nsteps * 1e3, 4), "ghost_depth": 8 * s,
+                        "computed_over_owned_nodes": round(local / npts, 4),
+                        "identical_to_single": bool(torch.equal(dec.get("p"), p_ref))}
+        dec.close()
+        del dec
+        torch.cuda.empty_cache()
+    return {"workload": f"layered512 pencil-yz 1x2x2 parts on one GPU, {warm} + {nsteps} timed steps", "unit": UNIT,
+            **out}
 
 
 def form_tblock(dev, nsteps=96, warm=8):
@@ -903,6 +960,8 @@ def main():
                     forms[f] = form_cpml_overhead(dev)
                 elif f == "tblock":
                     forms[f] = form_tblock(dev)
+                elif f == "decomp":
+                    forms[f] = form_decomp(dev)
                 elif f == "density":
                     forms[f] = form_density(dev)
                 elif f == "staggered":

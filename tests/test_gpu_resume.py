@@ -43,7 +43,7 @@ def test_resume_equals_uninterrupted_run():
     for (k, s), v in saved.items():
         c.set(k, v, s)
     c.set_time(stop)
-    assert c.time() == stop
+    assert c.time == stop
     c.step(nt - stop)
     c.sync()
     for k in FIELDS:
