@@ -37,21 +37,22 @@ __device__ __forceinline__ void cp1(unsigned char *dst, long long di, const unsi
     reinterpret_cast<E *>(dst)[di] = reinterpret_cast<const E *>(src)[si];
 }
 
-// One thread per (shot, node) of the box; E is the stored element (4 or 2 bytes).
+// One thread per node of a box row: x from blockIdx.x / threadIdx.x, the row
+// y from blockIdx.y, and (shot, z) from blockIdx.z, striding over the rest;
+// E is the stored element (4 or 2 bytes).
 template <typename E>
 __global__ void exchange_kernel(XDst D, XSide S, int z0, int y0, int x0, int bz, int by, int bx, int sz, int sy,
                                 int sx, int nshots)
 {
-    const long long nbox = (long long)bz * by * bx;
-    const long long total = nbox * nshots;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int shot = (int)(i / nbox);
-        const long long r = i - (long long)shot * nbox;
-        const int z = z0 + (int)(r / ((long long)by * bx));
-        const int y = y0 + (int)((r / bx) % by);
-        const int x = x0 + (int)(r % bx);
-        const int zs = z + sz, ys = y + sy, xs = x + sx;
+    const int x = x0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= x0 + bx)
+        return;
+    const int y = y0 + blockIdx.y;
+    const int xs = x + sx, ys = y + sy;
+    for (int q = blockIdx.z; q < bz * nshots; q += gridDim.z) {
+        const int shot = q / bz;
+        const int z = z0 + (q - shot * bz);
+        const int zs = z + sz;
         const long long di = shot * D.g.vol + (long long)z * D.g.plane + (long long)y * D.g.nxp + x;
         const long long si = shot * S.g.vol + (long long)zs * S.g.plane + (long long)ys * S.g.nxp + xs;
         cp1<E>(D.p, di, S.p, si);
@@ -92,17 +93,18 @@ cudaError_t launch_exchange(fdtd_ctx *dst, const fdtd_ctx *src, const int box[6]
         S.psip[d] = (const unsigned char *)src->psip[d];
     }
     const int bz = box[1] - box[0], by = box[3] - box[2], bx = box[5] - box[4];
-    const long long total = (long long)bz * by * bx * dst->d.nshots;
-    const int threads = 256;
-    const int blocks = (int)std::min<long long>((total + threads - 1) / threads, 152LL * 8);
+    const int threads = 128;
+    // rows of the box: x across threads, y across blockIdx.y (<= 65535 rows,
+    // the grid's y extent), (shot, z) across blockIdx.z with a stride
+    const dim3 grid((bx + threads - 1) / threads, by, (unsigned)std::min(bz * dst->d.nshots, 65535));
+    if (by > 65535)
+        return cudaErrorInvalidConfiguration;
     if (dst->es == 4)
-        exchange_kernel<uint32_t><<<blocks, threads, 0, dst->stream>>>(D, S, box[0], box[2], box[4], bz, by, bx,
-                                                                        shift[0], shift[1], shift[2],
-                                                                        dst->d.nshots);
+        exchange_kernel<uint32_t><<<grid, threads, 0, dst->stream>>>(D, S, box[0], box[2], box[4], bz, by, bx,
+                                                                      shift[0], shift[1], shift[2], dst->d.nshots);
     else
-        exchange_kernel<uint16_t><<<blocks, threads, 0, dst->stream>>>(D, S, box[0], box[2], box[4], bz, by, bx,
-                                                                        shift[0], shift[1], shift[2],
-                                                                        dst->d.nshots);
+        exchange_kernel<uint16_t><<<grid, threads, 0, dst->stream>>>(D, S, box[0], box[2], box[4], bz, by, bx,
+                                                                      shift[0], shift[1], shift[2], dst->d.nshots);
     return cudaGetLastError();
 }
 

@@ -13,8 +13,12 @@ p, v and the memory variables), and then every part advances s steps; the
 owned boxes then hold exactly the values of one undivided grid (s = 1 is the
 standard exchange, s > 1 the enlarged ghost region, Tab. 12).
 
-Here all parts share one GPU and one stream, so the exchange kernel reads the
-neighbour's memory directly and stream order sequences steps and exchanges.
+Here all parts share one GPU, each on a stream of its own, so the exchange
+kernel reads the neighbour's memory directly and the parts' steps run side by
+side as they would on separate GPUs.  Events order the phases: every part
+finishes its steps before any exchange reads it, and every exchange finishes
+before any part steps again (the parts update their pressure memory variables
+in place).
 Sources are injected by every part whose box (ghosts included) contains them,
 so that the ghost layers evolve as the grid does between exchanges; receivers
 are recorded by their owner only.  This module does argument marshalling:
@@ -113,13 +117,35 @@ class Decomposition:
         self.subs = []
         for part in geo:
             lshape = tuple(hi - lo for lo, hi in part["loc"])
+            st = torch.cuda.Stream(self.device)
             sim = Fdtd(lshape, h, dt, nshots=self.nshots, cpml_cells=part["cells"], storage=storage,
                        nt_max=self.nt_max, nrec_max=nrec_max, cpml_local=cpml_local, device=self.device,
-                       stream=self.stream)
-            self.subs.append(dict(sim=sim, own=part["own"], loc=part["loc"], rec_cols=None))
+                       stream=st)
+            self.subs.append(dict(sim=sim, stream=st, own=part["own"], loc=part["loc"], rec_cols=None))
         self.links = [(i, j, (ctypes.c_int * 6)(*box), (ctypes.c_int * 3)(*shift)) for i, j, box, shift in links]
         self.traces = None
         self.t = 0
+
+    # -- ordering of the parts' streams ------------------------------------------
+    def _parts_wait_main(self):
+        for sub in self.subs:
+            sub["stream"].wait_stream(self.stream)
+
+    def _main_waits_parts(self):
+        for sub in self.subs:
+            self.stream.wait_stream(sub["stream"])
+
+    def _barrier(self):
+        """Everything enqueued so far on any part's stream comes before what
+        any part enqueues next."""
+        evs = []
+        for sub in self.subs:
+            e = torch.cuda.Event()
+            e.record(sub["stream"])
+            evs.append(e)
+        for sub in self.subs:
+            for e in evs:
+                sub["stream"].wait_event(e)
 
     # -- set-up ----------------------------------------------------------------
     def _crop(self, vol, sub):
@@ -132,9 +158,11 @@ class Decomposition:
         maximum velocity (the scale one grid would use), so that exchanged
         values need no conversion."""
         self.c_max = float(vel.max())
-        for sub in self.subs:
+        boxes = [(self._crop(vel, sub), None if rho is None else self._crop(rho, sub)) for sub in self.subs]
+        self._parts_wait_main()   # the boxes are cut on the caller's stream
+        for sub, (v, r) in zip(self.subs, boxes):
             sub["sim"].set_velocity_scale(self.c_max)
-            sub["sim"].set_model(self._crop(vel, sub), None if rho is None else self._crop(rho, sub))
+            sub["sim"].set_model(v, r)   # synchronises the part's stream
 
     def set_staggered(self, on: bool = True):
         for sub in self.subs:
@@ -144,8 +172,10 @@ class Decomposition:
         """The local-velocity grading: every slab node's coefficients come
         from its own velocity and its face's layer, so each part computes
         them from its box of the model."""
-        for sub in self.subs:
-            sub["sim"].set_cpml_local(self._crop(vel, sub), R=R, kappa_max=kappa_max, alpha_frac=alpha_frac, q=q)
+        boxes = [self._crop(vel, sub) for sub in self.subs]
+        self._parts_wait_main()
+        for sub, v in zip(self.subs, boxes):
+            sub["sim"].set_cpml_local(v, R=R, kappa_max=kappa_max, alpha_frac=alpha_frac, q=q)
 
     def set_cpml(self, R=1e-8, kappa_max=5.0, alpha_frac=0.05, q=3, c_ref=None):
         """The grading of the whole grid: one reference velocity (the whole
@@ -158,6 +188,7 @@ class Decomposition:
         """Every part whose box holds a shot's source injects it (the others
         get a zero wavelet row for that shot at a node of their own)."""
         src = [tuple(int(v) for v in r) for r in src_zyx]
+        ws = []
         for sub in self.subs:
             loc = sub["loc"]
             rows, w = [], wavelet.clone()
@@ -168,7 +199,11 @@ class Decomposition:
                 else:
                     rows.append([0, 0, 0])
                     w[k].zero_()
-            sub["sim"].inject(rows, w.contiguous())
+            ws.append((sub, rows, w.contiguous()))
+        self._parts_wait_main()
+        for sub, rows, w in ws:
+            sub["sim"].inject(rows, w)
+        self._wavelets = ws   # kept alive until the parts have copied them
 
     def record(self, rec_zyx):
         """Receivers (global (z, y, x)); each is recorded by the part that
@@ -190,15 +225,21 @@ class Decomposition:
             a._check(a.lib.fdtd_exchange(a.ctx, b.ctx, box, shift))
 
     def step(self, n: int):
-        """Advance n steps: blocks of s steps, each after a ghost exchange."""
+        """Advance n steps: blocks of s steps, each after a ghost exchange.
+        The work is enqueued on the parts' streams, and the caller's stream
+        waits for it before this returns."""
+        self._parts_wait_main()
         done = 0
         while done < n:
             k = min(self.s, n - done)
+            self._barrier()
             self.exchange()
+            self._barrier()
             for sub in self.subs:
                 sub["sim"].step(k)
             done += k
         self.t += n
+        self._main_waits_parts()
         if self.traces is not None:
             for sub in self.subs:
                 if sub["rec_cols"]:
@@ -209,8 +250,10 @@ class Decomposition:
             sub["sim"].sync()
 
     def reset(self):
+        self._parts_wait_main()
         for sub in self.subs:
             sub["sim"].reset()
+        self._main_waits_parts()
         self.t = 0
 
     def get(self, which: str, shot=0) -> torch.Tensor:
@@ -218,7 +261,12 @@ class Decomposition:
         out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
         for sub in self.subs:
             loc, own = sub["loc"], sub["own"]
+            # the part writes its field on its own stream into a buffer of the
+            # caller's stream (which may reuse the previous part's buffer), so
+            # it waits for the caller's stream first and the caller for it after
+            sub["stream"].wait_stream(self.stream)
             f = sub["sim"].get(which, shot)
+            self.stream.wait_stream(sub["stream"])
             sl = tuple(slice(o[0] - l[0], o[1] - l[0]) for o, l in zip(own, loc))
             out[own[0][0]:own[0][1], own[1][0]:own[1][1], own[2][0]:own[2][1]] = f[sl]
         return out

@@ -131,6 +131,28 @@ def test_decomposed_forms_equal_single_grid(form):
     assert torch.equal(tr, tr_ref)
 
 
+def test_decomposed_large_grid_equals_single_grid():
+    # a grid large enough that the parts' kernels and read-outs overlap on
+    # their streams (ordering of steps, exchanges and read-outs by events)
+    from paper_2606_06910_gb300.decomp import Decomposition
+    from paper_2606_06910_gb300.fdtd import Fdtd
+    shape, cells, h, nt = (224, 200, 176), (20, 20, 20, 20, 20, 20), 10.0, 12
+    vel = torch.from_numpy(synth.layered_model(shape, seed=13)).cuda()
+    dt = 0.5 * h / float(vel.max())
+    wav = torch.from_numpy(synth.ricker(nt, dt, 40.0).astype(np.float32)[None, :]).cuda()
+    src = [[60, 99, 90]]
+    a = Fdtd(shape, h, dt, cpml_cells=cells, nt_max=nt)
+    b = Decomposition(shape, h, dt, parts=(2, 2, 2), s=2, cpml_cells=cells, nt_max=nt)
+    for sim in (a, b):
+        sim.set_model(vel)
+        sim.set_cpml(R=1e-8, c_ref=float(vel.max()))
+        sim.inject(src, wav)
+        sim.step(nt)
+    for k in FIELDS:
+        assert torch.equal(b.get(k), a.get(k)), k
+    b.close()
+
+
 def test_exchange_validates_its_arguments():
     from paper_2606_06910_gb300.fdtd import Fdtd
     a = Fdtd((20, 20, 20), 10.0, 1e-3, nt_max=4)
