@@ -145,16 +145,25 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def step_kernel_source_hash() -> str:
+    """Hash of the step kernel's device code: fdtd_step.cu and the shared
+    declarations of fdtd_internal.cuh up to the host-only context struct."""
+    csrc = os.path.join(ROOT, "paper_2606_06910_gb300", "csrc")
+    step = open(os.path.join(csrc, "fdtd_step.cu"), "rb").read()
+    inc = open(os.path.join(csrc, "fdtd_internal.cuh"), "rb").read()
+    cut = inc.find(b"// The opaque context behind fdtd_ctx*.")
+    return hashlib.sha256(step + (inc[:cut] if cut >= 0 else inc)).hexdigest()[:16]
+
+
 def step_kernel_traffic(storage: str, shape, variant: str = "plain"):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     scaled to this grid, or None when the kernel source changed since (forms
     other than the plain one are keyed "<storage>-<variant>")."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    srcs = [os.path.join(ROOT, "paper_2606_06910_gb300", "csrc", f) for f in ("fdtd_step.cu", "fdtd_internal.cuh")]
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    h = hashlib.sha256(b"".join(open(s, "rb").read() for s in srcs)).hexdigest()[:16]
+    h = step_kernel_source_hash()
     e = d.get(storage if variant == "plain" else f"{storage}-{variant}")
     if not e or e.get("kernel_sha") != h:
         return None

@@ -789,15 +789,17 @@ cudaError_t adjoint_step_fused(fdtd_ctx *c, const float *s_tape)
     FusedArgs a;
     a.g = c->g;
     a.tiles_x = c->tiles_x;
-    // z-chunks: as the forward step's, with the end chunks reaching 8 planes
-    // past the z slabs (the reach of lam_h_z)
+    // z-chunks: on large grids (where the forward step has end chunks) the
+    // end chunks reach 8 planes past the z slabs (the reach of lam_h_z) and
+    // the middle is cut into chunks of about azchunk_target planes
     a.zmid0 = 0;
     a.zmid1 = c->g.nz;
     a.zchunk = c->zchunk;
     if (c->zmid0 > 0 || c->zmid1 < c->g.nz) {
         const int e1 = c->g.lo[2] + 8, e2 = c->g.nz - c->g.hi[2] - 8;
-        if (e2 - e1 >= c->zchunk_mid) {
-            const int km = (e2 - e1 + c->zchunk_mid - 1) / c->zchunk_mid;
+        const int target = c->azchunk_target;
+        if (e2 - e1 >= target) {
+            const int km = (e2 - e1 + target - 1) / target;
             a.zmid0 = e1;
             a.zmid1 = e2;
             a.zchunk = (e2 - e1 + km - 1) / km;

@@ -342,6 +342,7 @@ struct fdtd_ctx {
     int es;                 // bytes per stored element
     int tiles_x, tiles_y, zchunk, nzchunks;   // uniform z-chunks (adjoint kernels)
     int zmid0, zmid1, zchunk_mid;             // forward step chunks (see StepArgs::zmid0)
+    int azchunk_target;                       // planes per middle chunk of the fused adjoint
     float vscale;           // stored velocity = vscale * v (impedance scaling for 16-bit)
     float vscale_req;       // fdtd_set_velocity_scale: the scale 16-bit storage uses (0: the model's maximum)
     float sscale;           // every stored field is multiplied by sscale (2^10 for FP16, else 1)
