@@ -293,6 +293,15 @@ int fdtd_reset(fdtd_ctx *ctx);
 /* Current time index (steps taken since create/reset). */
 int fdtd_time(const fdtd_ctx *ctx, int *t);
 
+/* Divergence detection (off by default): after every `every` steps of
+ * fdtd_step_n the library sums p^2 over every node of every shot in FP64 on
+ * the device; a sum that is not finite, or above `limit` when limit > 0,
+ * raises a device error that the next synchronising call (fdtd_sync)
+ * reports as EDIVERGED.  No host synchronisation; one reduction over p per
+ * check (4 B per node in FP32).  every = 0 turns it off.  EINVAL for
+ * every < 0 or a NaN limit. */
+int fdtd_set_divergence_check(fdtd_ctx *ctx, int every, double limit);
+
 /* Set the time index (resume: with the fields restored by fdtd_set_field, a
  * run continues from step t, sampling wavelets and recording traces at t and
  * after).  EINVAL if t < 0; EUNSUPPORTED for a context with checkpoints,

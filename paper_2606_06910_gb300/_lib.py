@@ -68,6 +68,7 @@ _SIGS = {
     "fdtd_time": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
     "fdtd_sync": (c_int, [c_void_p]),
     "fdtd_set_time": (c_int, [c_void_p, c_int]),
+    "fdtd_set_divergence_check": (c_int, [c_void_p, c_int, c_double]),
     "fdtd_energy": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
     "fdtd_misfit": (c_int, [c_void_p, c_void_p, c_int, c_void_p, ctypes.POINTER(c_double)]),
     "fdtd_misfit_noalloc": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_void_p,

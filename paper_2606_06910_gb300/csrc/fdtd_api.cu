@@ -21,6 +21,7 @@ cudaError_t launch_field(const fdtd_ctx *c, bool get, void *internal, float *den
                          bool is_f32, const float *kscale);
 cudaError_t launch_energy(const fdtd_ctx *c, const void *p, const int *box);
 cudaError_t launch_misfit(const fdtd_ctx *c, const float *dobs, int nt, float *resid);
+cudaError_t launch_divergence_check(const fdtd_ctx *c, double limit);
 cudaError_t launch_ska_to_coef(const fdtd_ctx *c, const float *ska, int L);
 cudaError_t launch_local_coef(const fdtd_ctx *c, const float *vel, double R, double kmax, double afrac, int q);
 cudaError_t launch_ska_backward(const fdtd_ctx *c, const float *ska, const float *gprof, int L, float *gska);
@@ -1208,6 +1209,7 @@ int fdtd_step_n(fdtd_ctx *c, int n)
                     break;
             }
         int st;
+        const int t_before = c->t;
         if (m > 0) {
             st = launch_blocks(c, m);
             i += m * k;
@@ -1217,7 +1219,21 @@ int fdtd_step_n(fdtd_ctx *c, int n)
         }
         if (st)
             return st;
+        // divergence check when a multiple of div_every was reached
+        if (c->div_every > 0 && c->t / c->div_every > t_before / c->div_every)
+            CUDA_TRY(c, launch_divergence_check(c, c->div_limit));
     }
+    return FDTD_OK;
+}
+
+int fdtd_set_divergence_check(fdtd_ctx *c, int every, double limit)
+{
+    if (!c)
+        return FDTD_EINVAL;
+    if (every < 0 || std::isnan(limit))
+        return fail(c, FDTD_EINVAL, "every must be >= 0 and limit a number");
+    c->div_every = every;
+    c->div_limit = limit > 0.0 ? limit * (double)c->sscale * (double)c->sscale : HUGE_VAL;
     return FDTD_OK;
 }
 
@@ -1440,7 +1456,7 @@ int fdtd_sync(fdtd_ctx *c)
     if (err & ERR_TIMEOUT)
         return fail(c, FDTD_ETIMEOUT, "a bounded device-side wait gave up");
     if (err & ERR_NONFINITE)
-        return fail(c, FDTD_EDIVERGED, "non-finite values");
+        return fail(c, FDTD_EDIVERGED, "the field diverged (non-finite values, or the energy above the check's limit)");
     return FDTD_OK;
 }
 

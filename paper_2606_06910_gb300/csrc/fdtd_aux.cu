@@ -303,6 +303,27 @@ cudaError_t launch_energy(const fdtd_ctx *c, const void *p, const int *box)
     return cudaGetLastError();
 }
 
+// Divergence check: sum of p^2 over every node of every shot (the energy
+// reduction over a box whose z range runs through the shots, which follow
+// each other in memory), then one thread raises ERR_NONFINITE if the sum is
+// not finite or above `limit` (in stored units).
+__global__ void divergence_flag_kernel(const double *sum, double limit, unsigned *err)
+{
+    const double s = *sum;
+    if (!(s == s) || isinf(s) || s > limit)
+        atomicOr(err, ERR_NONFINITE);
+}
+
+cudaError_t launch_divergence_check(const fdtd_ctx *c, double limit)
+{
+    const int box[6] = {0, c->g.nz * c->d.nshots, 0, c->g.ny, 0, c->g.nx};
+    const cudaError_t e = launch_energy(c, c->p[c->cur], box);
+    if (e != cudaSuccess)
+        return e;
+    divergence_flag_kernel<<<1, 1, 0, c->stream>>>(c->red + RED_BLOCKS, limit, c->err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_misfit(const fdtd_ctx *c, const float *dobs, int nt, float *resid)
 {
     misfit_kernel<<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(c->traces, dobs, resid, c->d.nshots, nt, c->d.nt_max,

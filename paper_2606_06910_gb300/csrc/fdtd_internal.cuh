@@ -348,6 +348,8 @@ struct fdtd_ctx {
     float sscale;           // every stored field is multiplied by sscale (2^10 for FP16, else 1)
     float c_max, c_min;
     int t;                  // time index
+    int div_every;          // fdtd_set_divergence_check: every this many steps (0: off)
+    double div_limit;       // energy limit in stored units (infinity: non-finite only)
     int cur;                // ping-pong buffer holding the current state
     bool model_set, cpml_set, cpml_ska;
     int nrec;

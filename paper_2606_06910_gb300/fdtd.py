@@ -200,6 +200,11 @@ class Fdtd:
     def sync(self):
         self._check(self.lib.fdtd_sync(self.ctx))
 
+    def set_divergence_check(self, every: int, limit: float = 0.0):
+        """Every `every` steps, flag a non-finite sum of p^2 (or one above
+        `limit` if > 0); sync() then raises EDIVERGED.  0 turns it off."""
+        self._check(self.lib.fdtd_set_divergence_check(self.ctx, int(every), float(limit)))
+
     def set_time(self, t: int):
         """Time index to continue from (resume after set() of every field)."""
         self._check(self.lib.fdtd_set_time(self.ctx, int(t)))

@@ -155,3 +155,11 @@ def test_cpml_grading_matches_oracle_profile(lib, L, q, R, kmax, af):
     assert lib.fdtd_cpml_grading(0, h, c, R, kmax, af, q, out) == _lib.EINVAL
     assert lib.fdtd_cpml_grading(L, h, c, 2.0, kmax, af, q, out) == _lib.EINVAL
     assert lib.fdtd_cpml_grading(L, h, c, R, kmax, af, q, None) == _lib.EINVAL
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    assert lib.fdtd_set_divergence_check(None, 1, 0.0) == _lib.EINVAL
+    assert lib.fdtd_set_time(None, 3) == _lib.EINVAL
+    assert lib.fdtd_set_velocity_scale(None, 1.0) == _lib.EINVAL
+    assert lib.fdtd_set_timing(None, 1) == _lib.EINVAL
+    assert lib.fdtd_exchange(None, None, None, None) == _lib.EINVAL
