@@ -16,12 +16,11 @@ namespace fdtd {
 __global__ void model_kernel(const float *__restrict__ vel, const float *__restrict__ rho, float *__restrict__ kdt,
                              float *__restrict__ nbr, Geom g, double dt, double vs, unsigned *minmax)
 {
-    const long long n = g.vol;
     unsigned vmin = 0x7f800000u, vmax = 0u, bad = 0u;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.nxp);
-        const long long zy = i / g.nxp;
+    // rows (z, y) across blocks, x across threads: no division per node
+    for (long long zy = blockIdx.x; zy < (long long)g.nz * g.ny; zy += gridDim.x)
+    for (int x = threadIdx.x; x < g.nxp; x += blockDim.x) {
+        const long long i = zy * g.nxp + x;
         if (x >= g.nx) {
             kdt[i] = 0.f;
             if (rho)
@@ -61,15 +60,13 @@ __global__ void local_coef_kernel(const float *__restrict__ vel, Geom g, int d, 
                                   double kmax, double afrac, int q, float *__restrict__ lb, float *__restrict__ la,
                                   unsigned *bad)
 {
-    const long long n = (long long)g.nz * g.ny * g.nx;
     const int na = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
     const int lo = g.lo[d], hi = g.hi[d];
     unsigned nbad = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.nx);
-        const long long zy = i / g.nx;
-        const int y = (int)(zy % g.ny), z = (int)(zy / g.ny);
+    for (long long zy = blockIdx.x; zy < (long long)g.nz * g.ny; zy += gridDim.x)
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+        const long long i = zy * g.nx + x;
+        const int z = (int)(zy / g.ny), y = (int)(zy - (long long)z * g.ny);
         const int j = d == 0 ? x : (d == 1 ? y : z);
         if (!in_slab(j, na, lo, hi))
             continue;
@@ -133,12 +130,10 @@ template <typename T>
 __global__ void get_field_kernel(const T *__restrict__ src, float *__restrict__ dst, Geom g, int kind, float scale,
                                  const float *__restrict__ div)
 {
-    const long long n = (long long)g.nz * g.ny * g.nx;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.nx);
-        const int y = (int)((i / g.nx) % g.ny);
-        const int z = (int)(i / ((long long)g.nx * g.ny));
+    for (long long zy = blockIdx.x; zy < (long long)g.nz * g.ny; zy += gridDim.x)
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+        const long long i = zy * g.nx + x;
+        const int z = (int)(zy / g.ny), y = (int)(zy - (long long)z * g.ny);
         float v = 0.f;
         if (kind == 0) {
             const long long o = (long long)z * g.plane + (long long)y * g.nxp + x;
@@ -160,12 +155,10 @@ template <typename T>
 __global__ void set_field_kernel(T *__restrict__ dstf, const float *__restrict__ src, Geom g, int kind, float scale,
                                  const float *__restrict__ mul)
 {
-    const long long n = (long long)g.nz * g.ny * g.nx;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.nx);
-        const int y = (int)((i / g.nx) % g.ny);
-        const int z = (int)(i / ((long long)g.nx * g.ny));
+    for (long long zy = blockIdx.x; zy < (long long)g.nz * g.ny; zy += gridDim.x)
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+        const long long i = zy * g.nx + x;
+        const int z = (int)(zy / g.ny), y = (int)(zy - (long long)z * g.ny);
         if (kind == 0) {
             const long long o = (long long)z * g.plane + (long long)y * g.nxp + x;
             Io<T>::st1(dstf + o, mul ? src[i] * scale * mul[o] : src[i] * scale);
@@ -237,16 +230,16 @@ template <typename T>
 __global__ void energy_kernel(const T *__restrict__ p, Geom g, int z0, int z1, int y0, int y1, int x0, int x1,
                               double *part)
 {
-    const long long nxb = x1 - x0, nyb = y1 - y0, nzb = z1 - z0;
-    const long long n = nxb * nyb * nzb;
+    const int nyb = y1 - y0;
     double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = x0 + (int)(i % nxb);
-        const int y = y0 + (int)((i / nxb) % nyb);
-        const int z = z0 + (int)(i / (nxb * nyb));
-        const double v = Io<T>::ld1(p + (long long)z * g.plane + (long long)y * g.nxp + x);
-        acc += v * v;
+    // rows of the box across blocks, x across threads
+    for (long long r = blockIdx.x; r < (long long)(z1 - z0) * nyb; r += gridDim.x) {
+        const int z = z0 + (int)(r / nyb), y = y0 + (int)(r % nyb);
+        const T *row = p + (long long)z * g.plane + (long long)y * g.nxp;
+        for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
+            const double v = Io<T>::ld1(row + x);
+            acc += v * v;
+        }
     }
     const double s = block_sum(acc);
     if (threadIdx.x == 0)
