@@ -268,33 +268,59 @@ def run_ours(args, rank, world, local):
     peak, peak_kind = measured_peaks()
     traffic = step_kernel_traffic(args.storage, shape, variant)
 
-    # end to end through the public API: pinned host model + wavelet in,
-    # final pressure snapshot out, every step
+    # end to end through the public API: every step copies its model and
+    # wavelet in from pinned host memory and its pressure snapshot out to
+    # pinned host memory.  The copies run on a stream of their own, double
+    # buffered: step k+1's inputs go up and step k-1's snapshot comes down
+    # while step k computes; the timed region ends when the last snapshot is
+    # on the host.
     e2e = None
     if not args.no_e2e and variant == "plain":
         vel_pin = torch.from_numpy(vel_h).pin_memory()
         wav_pin = torch.from_numpy(wav_h).pin_memory()
-        snap_pin = torch.empty(shape, dtype=torch.float32).pin_memory()
-        vel_d = torch.empty_like(vel)
-        wav_d = torch.empty_like(wav)
-        snap_d = torch.empty(shape, dtype=torch.float32, device=dev)
+        snap_pin = [torch.empty(shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+        vel_d = [torch.empty_like(vel) for _ in range(2)]
+        wav_d = [torch.empty_like(wav) for _ in range(2)]
+        snap_d = [torch.empty(shape, dtype=torch.float32, device=dev) for _ in range(2)]
+        copy = torch.cuda.Stream(dev)
         ksteps = args.steps
+        up = [torch.cuda.Event() for _ in range(2)]
+        done = [torch.cuda.Event() for _ in range(2)]
+        down = [torch.cuda.Event() for _ in range(2)]
+
+        def upload(k):
+            b = k % 2
+            with torch.cuda.stream(copy):
+                copy.wait_event(done[b])          # step k-2 no longer reads buffer b
+                vel_d[b].copy_(vel_pin, non_blocking=True)
+                wav_d[b].copy_(wav_pin, non_blocking=True)
+                up[b].record(copy)
+
         torch.cuda.synchronize(dev)
         e0 = time.perf_counter()
-        for _ in range(ksteps):
-            vel_d.copy_(vel_pin, non_blocking=True)
-            wav_d.copy_(wav_pin, non_blocking=True)
-            sim.set_model(vel_d)
-            sim.inject(src, wav_d)
+        upload(0)
+        for k in range(ksteps):
+            b = k % 2
+            stream.wait_event(up[b])
+            stream.wait_event(down[b])            # snapshot k-2 has left buffer b
+            sim.set_model(vel_d[b])               # synchronises the compute stream
+            if k + 1 < ksteps:
+                upload(k + 1)
+            sim.inject(src, wav_d[b])
             sim.reset()
             sim.step(nt)
-            sim.get("p", 0, snap_d)
-            snap_pin.copy_(snap_d, non_blocking=True)
-            torch.cuda.synchronize(dev)
+            sim.get("p", 0, snap_d[b])
+            done[b].record(stream)
+            with torch.cuda.stream(copy):
+                copy.wait_event(done[b])
+                snap_pin[b].copy_(snap_d[b], non_blocking=True)
+                down[b].record(copy)
+        torch.cuda.synchronize(dev)
         e_s = time.perf_counter() - e0
         e2e = {"value": round(world * npts * nt * ksteps / e_s / 1e6, 2), "unit": UNIT,
                "h2d_bytes_per_step": int(vel_pin.numel() * 4 + wav_pin.numel() * 4 + src.size * 4),
-               "d2h_bytes_per_step": int(snap_pin.numel() * 4)}
+               "d2h_bytes_per_step": int(snap_pin[0].numel() * 4),
+               "copies": "on their own stream, double buffered, overlapping the neighbouring steps"}
     sim.sync()
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
