@@ -281,9 +281,11 @@ int fdtd_set_field(fdtd_ctx *ctx, int which, int shot, const float *src_dev);
  * in the d-slabs of both).  Both must have the same storage, shots and form
  * and the same time index (ESTATE otherwise); EINVAL if a box leaves either
  * grid, or if the two store velocities at different scales (see
- * fdtd_set_velocity_scale).  The copy is one kernel on dst's stream that reads src's arrays
- * directly: src's last step must be complete or on the same stream.  The
- * adjoint state and checkpoints are not exchanged. */
+ * fdtd_set_velocity_scale).  The copy is one kernel on dst's stream that
+ * reads src's arrays directly: src's last step must be complete or on the
+ * same stream.  The adjoint state and checkpoints are not exchanged.  Both
+ * contexts must live on the same GPU (EUNSUPPORTED otherwise: parts on
+ * several GPUs would need peer access, which this build does not set up). */
 int fdtd_exchange(fdtd_ctx *dst, const fdtd_ctx *src, const int box[6], const int shift[3]);
 
 /* Zero every field and memory variable, time index 0 (model, CPML, source and

@@ -827,6 +827,10 @@ int fdtd_create(const fdtd_desc *desc, void *workspace, size_t workspace_bytes, 
     c->tiles_x = L.tiles_x;
     c->tiles_y = L.tiles_y;
     c->kr[0] = c->kr[1] = c->kr[2] = 1.0;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return FDTD_ECUDA;
+    }
     c->vscale = 1.f;
     // FP16 keeps the whole state scaled by 2^10 (exact): small late-time
     // fields stay out of the FP16 subnormal range; the update is linear, so
@@ -1515,6 +1519,9 @@ int fdtd_exchange(fdtd_ctx *dst, const fdtd_ctx *src, const int box[6], const in
         return fail(dst, FDTD_EINVAL, "source and destination are the same context");
     if (dst->d.storage != src->d.storage || dst->d.nshots != src->d.nshots || dst->staggered != src->staggered)
         return fail(dst, FDTD_EINVAL, "contexts differ in storage, shots or form");
+    if (dst->device != src->device)
+        return fail(dst, FDTD_EUNSUPPORTED, "contexts on different GPUs (devices %d and %d) need peer access, "
+                                            "which this build does not set up", src->device, dst->device);
     if (dst->t != src->t)
         return fail(dst, FDTD_ESTATE, "contexts are at different time indices (%d, %d)", dst->t, src->t);
     if (dst->vscale != src->vscale || dst->sscale != src->sscale)

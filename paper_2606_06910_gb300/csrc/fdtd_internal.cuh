@@ -347,6 +347,7 @@ struct fdtd_ctx {
     float vscale_req;       // fdtd_set_velocity_scale: the scale 16-bit storage uses (0: the model's maximum)
     float sscale;           // every stored field is multiplied by sscale (2^10 for FP16, else 1)
     float c_max, c_min;
+    int device;             // the CUDA device current at fdtd_create
     int t;                  // time index
     int div_every;          // fdtd_set_divergence_check: every this many steps (0: off)
     double div_limit;       // energy limit in stored units (infinity: non-finite only)
