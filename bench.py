@@ -296,6 +296,13 @@ def run_ours(args, rank, world, local):
                 wav_d[b].copy_(wav_pin, non_blocking=True)
                 up[b].record(copy)
 
+        def download(k):
+            b = k % 2
+            with torch.cuda.stream(copy):
+                copy.wait_event(done[b])          # step k's snapshot is in buffer b
+                snap_pin[b].copy_(snap_d[b], non_blocking=True)
+                down[b].record(copy)
+
         torch.cuda.synchronize(dev)
         e0 = time.perf_counter()
         upload(0)
@@ -304,6 +311,11 @@ def run_ours(args, rank, world, local):
             stream.wait_event(up[b])
             stream.wait_event(down[b])            # snapshot k-2 has left buffer b
             sim.set_model(vel_d[b])               # synchronises the compute stream
+            # the previous snapshot goes down, and the next inputs go up, while
+            # this step computes; issued after set_model, whose small read-back
+            # then does not queue behind a large copy
+            if k >= 1:
+                download(k - 1)
             if k + 1 < ksteps:
                 upload(k + 1)
             sim.inject(src, wav_d[b])
@@ -311,10 +323,7 @@ def run_ours(args, rank, world, local):
             sim.step(nt)
             sim.get("p", 0, snap_d[b])
             done[b].record(stream)
-            with torch.cuda.stream(copy):
-                copy.wait_event(done[b])
-                snap_pin[b].copy_(snap_d[b], non_blocking=True)
-                down[b].record(copy)
+        download(ksteps - 1)
         torch.cuda.synchronize(dev)
         e_s = time.perf_counter() - e0
         e2e = {"value": round(world * npts * nt * ksteps / e_s / 1e6, 2), "unit": UNIT,
