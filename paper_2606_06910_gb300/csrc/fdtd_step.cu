@@ -91,9 +91,34 @@ struct Coef {
     float2 cp[4], cn[4];
 };
 
-// centred derivative from aligned neighbours: m[l-1] = f(-l), p[l-1] = f(+l)
+// centred derivative from aligned neighbours: m[l-1] = f(-l), p[l-1] = f(+l).
+// kSplit: two independent chains (l = 1, 2 and l = 3, 4) and their sum, which
+// shortens the dependency chain; the 16-bit forms, whose instruction stream
+// dominates their time, use it (FP32 keeps the single chain, which measured
+// faster there)
+template <bool kSplit = false>
 __device__ __forceinline__ V4 dnb(const V4 *m, const V4 *p, const Coef &C)
 {
+    if (kSplit) {
+        V4 r, s;
+        r.a = mul2(C.cp[0], p[0].a);
+        r.b = mul2(C.cp[0], p[0].b);
+        s.a = mul2(C.cp[2], p[2].a);
+        s.b = mul2(C.cp[2], p[2].b);
+        r.a = fma2(C.cn[0], m[0].a, r.a);
+        r.b = fma2(C.cn[0], m[0].b, r.b);
+        s.a = fma2(C.cn[2], m[2].a, s.a);
+        s.b = fma2(C.cn[2], m[2].b, s.b);
+        r.a = fma2(C.cp[1], p[1].a, r.a);
+        r.b = fma2(C.cp[1], p[1].b, r.b);
+        s.a = fma2(C.cp[3], p[3].a, s.a);
+        s.b = fma2(C.cp[3], p[3].b, s.b);
+        r.a = fma2(C.cn[1], m[1].a, r.a);
+        r.b = fma2(C.cn[1], m[1].b, r.b);
+        s.a = fma2(C.cn[3], m[3].a, s.a);
+        s.b = fma2(C.cn[3], m[3].b, s.b);
+        return V4{add2(r.a, s.a), add2(r.b, s.b)};
+    }
     V4 r;
     r.a = mul2(C.cp[0], p[0].a);
     r.b = mul2(C.cp[0], p[0].b);
@@ -143,8 +168,19 @@ __device__ __forceinline__ V4 dx4(const V4 &u, const V4 &v, const V4 &w, const C
 // The same two operations on one pair of nodes, with the operation order of
 // the first pair of dnb / dx4, so that a recomputed halo pair equals what the
 // neighbouring tile computes for its own nodes, bit for bit.
+template <bool kSplit = false>
 __device__ __forceinline__ float2 dnb2(const float2 *m, const float2 *p, const Coef &C)
 {
+    if (kSplit) {   // the order of dnb<true>
+        float2 r = mul2(C.cp[0], p[0]), s = mul2(C.cp[2], p[2]);
+        r = fma2(C.cn[0], m[0], r);
+        s = fma2(C.cn[2], m[2], s);
+        r = fma2(C.cp[1], p[1], r);
+        s = fma2(C.cp[3], p[3], s);
+        r = fma2(C.cn[1], m[1], r);
+        s = fma2(C.cn[3], m[3], s);
+        return add2(r, s);
+    }
     float2 r = mul2(C.cp[0], p[0]);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
@@ -289,7 +325,7 @@ __device__ __forceinline__ void tape4(float *tape, long long idx, int off, const
 // slot j: pq[j] = p(t + j), vzq[j] = v'_z(t - 4 + j); the queues shift by one
 // slot per plane.  kStag: v_z[t + 4] sits at t + 4.5 and the pressure at t
 // reads v_z at t - 4 .. t + 3 (the staggered neighbour sets).
-template <bool kStag, typename Zvel>
+template <bool kStag, bool kSplit, typename Zvel>
 __device__ __forceinline__ void zblock(V4 (&pq)[9], V4 (&vzq)[9], const V4 &pnew, const Coef &C, Zvel &&zvel,
                                        V4 &pt, V4 &hz)
 {
@@ -298,14 +334,14 @@ __device__ __forceinline__ void zblock(V4 (&pq)[9], V4 (&vzq)[9], const V4 &pnew
     {
         const V4 m[4] = {pq[kStag ? 4 : 3], pq[kStag ? 3 : 2], pq[kStag ? 2 : 1], pq[kStag ? 1 : 0]};
         const V4 p[4] = {pq[5], pq[6], pq[7], pq[8]};
-        gz = dnb(m, p, C);
+        gz = dnb<kSplit>(m, p, C);
     }
     pt = pq[0];
     vzq[8] = zvel(gz);
     {
         const V4 m[4] = {vzq[3], vzq[2], vzq[1], vzq[0]};
         const V4 p[4] = {vzq[kStag ? 4 : 5], vzq[kStag ? 5 : 6], vzq[kStag ? 6 : 7], vzq[kStag ? 7 : 8]};
-        hz = dnb(m, p, C);
+        hz = dnb<kSplit>(m, p, C);
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -354,6 +390,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                                           float (*sCxv)[TX + 8], float (*sCyv)[TY + 8])
 {
     using L = StageLayout<T>;
+    constexpr bool kSplit = sizeof(T) == 2;   // see dnb
     float *svx = reinterpret_cast<float *>(smem + NSTAGE * L::BYTES);
     float *svy = svx + L::SVX_FLOATS;
     uint64_t *bar = reinterpret_cast<uint64_t *>(svy + L::SVY_FLOATS);
@@ -623,7 +660,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
             return vzn;
         };
         V4 pt, hz4;
-        zblock<kStag>(pq, vzq, pnew, C, zvel, pt, hz4);
+        zblock<kStag, kSplit>(pq, vzq, pnew, C, zvel, pt, hz4);
 
         if (ok && active) {
             const unsigned char *Sp = S + L::OFF_P;   // p plane, origin (x0 - 8, y0 - 8)
@@ -660,7 +697,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     m[l - 1] = lds<T>(Sp, (ly - l + (kStag ? 1 : 0)) * L::PW + lx);
                     p[l - 1] = lds<T>(Sp, (ly + l) * L::PW + lx);
                 }
-                V4 g = dnb(m, p, C);
+                V4 g = dnb<kSplit>(m, p, C);
                 if (own_y) {
                     const long long iy = slab_index(G, 1, t, gy, gx);
                     const V4 psvy = ldg_v4(psiv_in[1] + iy);
@@ -687,7 +724,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     m[l - 1] = lds2<T>(Sp, (ly - l + (kStag ? 1 : 0)) * L::PW + lx);
                     p[l - 1] = lds2<T>(Sp, (ly + l) * L::PW + lx);
                 }
-                float2 g = dnb2(m, p, C);
+                float2 g = dnb2<kSplit>(m, p, C);
                 const int r = yh_y - y0 + 4;
                 if (halo_psi_y) {
                     const long long ih = slab_index(G, 1, t, yh_y, yh_x);
@@ -747,7 +784,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
                     m[l - 1] = ldsf(svy + (ty + 4 - l) * TX + 4 * tx);
                     p[l - 1] = ldsf(svy + (ty + 4 + l - (kStag ? 1 : 0)) * TX + 4 * tx);
                 }
-                hy4 = dnb(m, p, C);
+                hy4 = dnb<kSplit>(m, p, C);
             }
             if (own_x) {
                 const int cx = 4 * tx + 4;
