@@ -36,6 +36,15 @@ METRIC = "million output points/s and % of HBM peak, plain FP32 vs chosen forms"
 UNIT = "Mpoints/s"
 
 
+def cells_arg(text: str):
+    v = [int(x) for x in text.split(",")]
+    if len(v) == 1:
+        v = v * 6
+    if len(v) != 6 or min(v) < 0:
+        raise argparse.ArgumentTypeError("one count or six counts >= 0")
+    return tuple(v)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -45,7 +54,9 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--preset", default="layered512")
     ap.add_argument("--nt", type=int, default=None, help="time steps per bench step (default: the workload's)")
-    ap.add_argument("--cells", type=int, default=None, help="override CPML cells per face (0: no CPML)")
+    ap.add_argument("--cells", type=cells_arg, default=None,
+                    help="override CPML cells: one count for every face (0: no CPML), or six comma-separated "
+                         "counts -x,+x,-y,+y,-z,+z (profiling runs of one axis' layer)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
@@ -196,7 +207,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(dev)
     w = synth.preset(args.preset)
     nt = args.nt or w.nt
-    cells = w.cpml_cells if args.cells is None else (args.cells,) * 6
+    cells = w.cpml_cells if args.cells is None else args.cells
     shape = w.shape
     vel_h = w.velocity()
     src = w.sources()
@@ -886,7 +897,8 @@ def state_gb(shape, storage):
 
 
 def workload_config(args, shape, cells, nt, world):
-    out = {"workload": f"{args.preset}: {shape[0]}^3 layered 1500-4500 m/s, CPML {cells[0]} cells, "
+    cdesc = f"{cells[0]} cells" if len(set(cells)) == 1 else f"cells {','.join(map(str, cells))} (-x,+x,-y,+y,-z,+z)"
+    out = {"workload": f"{args.preset}: {shape[0]}^3 layered 1500-4500 m/s, CPML {cdesc}, "
                        f"R=1e-8, 10 Hz Ricker, {nt} time steps per bench step",
            "grid": list(shape), "time_steps_per_step": nt, "cpml_cells": list(cells),
            "storage": args.storage, "parallelism": f"replicas x{world}",
@@ -907,7 +919,7 @@ def run_reference(args, rank, world):
     from paper_2606_06910_gb300 import synth
     oracle.build()
     w = synth.preset(args.preset)
-    cells = w.cpml_cells if args.cells is None else (args.cells,) * 6
+    cells = w.cpml_cells if args.cells is None else args.cells
     nt = args.nt or w.nt
     vel = w.velocity().astype(np.float64)
     g = O.Grid(vel * vel, w.h, w.dt, O.make_profiles(w.shape, cells, w.h, w.dt, w.c_max, R=w.R))
