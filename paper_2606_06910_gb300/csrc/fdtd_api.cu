@@ -542,6 +542,8 @@ StepArgs base_args(const fdtd_ctx *c)
     memset(&a, 0, sizeof(a));
     a.g = c->g;
     a.tiles_x = c->tiles_x;
+    a.tiles_y = c->tiles_y;
+    x_layer_columns(c->g.nx, c->g.lo[0], c->g.hi[0], TX, &a.xcol_lo, &a.xcol_hi);
     a.zchunk = c->zchunk_mid;
     a.zbase = 0;
     a.zend = c->g.nz;

@@ -282,6 +282,25 @@ __host__ __device__ __forceinline__ long long slab_index(const Geom &g, int d, i
     return ((long long)slab_coord(z, g.nz, g.lo[2], g.hi[2]) * g.ny + y) * g.nxp + x;
 }
 
+// Tile columns (of width tx nodes) whose nodes or 4-node derivative reach
+// meet the x layers: the first *nlo and the last *nhi columns; both 0 when the
+// grid has no x layers or every column meets them.
+__host__ __device__ __forceinline__ void x_layer_columns(int nx, int lo, int hi, int tx, int *nlo, int *nhi)
+{
+    const int ncol = (nx + tx - 1) / tx;
+    int a = lo > 0 ? (lo + 4 + tx - 1) / tx : 0;
+    int b = 0;
+    if (hi > 0) {
+        // columns c with (c + 1) tx + 4 > nx - hi, i.e. c >= floor((nx - hi - 4) / tx)
+        const int first = nx - hi - 4 > 0 ? (nx - hi - 4) / tx : 0;
+        b = first < ncol ? ncol - first : 0;
+    }
+    if (a + b >= ncol)
+        a = b = 0;
+    *nlo = a;
+    *nhi = b;
+}
+
 // x-slab layout for a grid with nx nodes and lo / hi cells (host and tests)
 __host__ __device__ __forceinline__ void x_slab_layout(int nx, int lo, int hi, int *xhi, int *w0)
 {
@@ -299,7 +318,8 @@ __host__ __device__ __forceinline__ void x_slab_layout(int nx, int lo, int hi, i
 // Arguments of the fused forward step kernel (one launch = one time step).
 struct StepArgs {
     Geom g;
-    int tiles_x, zchunk;
+    int tiles_x, tiles_y, zchunk;
+    int xcol_lo, xcol_hi;           // tile columns at the low / high x face that meet the x layers
     int zbase, zend;                // z range of this launch: [zbase, zend)
     int zmid0, zmid1;               // chunks: [zbase, zmid0) if not empty, then zchunk planes per CTA
                                     // over [zmid0, zmid1), then [zmid1, zend) if not empty

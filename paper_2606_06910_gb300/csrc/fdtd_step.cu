@@ -382,6 +382,24 @@ __host__ __device__ __forceinline__ int chunk_count(const StepArgs &A)
 // coefficients sCxv, sCyv, A.cbv.. (the node tables otherwise).  kLocal
 // takes b and a of every slab node from the per-node tables A.lb, A.la
 // (local-velocity grading; 1/kappa stays the 1D table).
+// Launch order of the tiles within a z-chunk row: the tiles of the columns
+// that meet the x layers come first (row-major), then the others.  Those
+// tiles carry the x memory variables and run slower than their neighbours;
+// started first, they stay level with them along z, so that the halo lines
+// both read are still in L2 (row-major order alone let them fall behind).
+__device__ __forceinline__ int tile_of_block(const StepArgs &A, int b)
+{
+    const int e = A.xcol_lo + A.xcol_hi, m = A.tiles_x - e;
+    if (e == 0)
+        return b;
+    if (b < e * A.tiles_y) {
+        const int k = b % e;
+        return (b / e) * A.tiles_x + (k < A.xcol_lo ? k : m + k);
+    }
+    b -= e * A.tiles_y;
+    return (b / m) * A.tiles_x + A.xcol_lo + b % m;
+}
+
 template <typename T, bool kEdge, bool kRho, bool kStag, bool kLocal>
 __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorMap &mPq, const CUtensorMap &mVX,
                                           const CUtensorMap &mVY, const CUtensorMap &mVZ, const CUtensorMap &mK,
@@ -398,7 +416,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap &mP, const CUtensorM
     const Geom &G = A.g;
     const int tid = threadIdx.x;
     const int tx = tid % (TX / 4), ty = tid / (TX / 4);
-    const int tile = blockIdx.x;
+    const int tile = tile_of_block(A, blockIdx.x);
     const int x0 = (tile % A.tiles_x) * TX, y0 = (tile / A.tiles_x) * TY;
     const int shot = blockIdx.z;
     const int gx = x0 + 4 * tx, gy = y0 + ty;
@@ -878,7 +896,8 @@ __global__ void __launch_bounds__(NTHREADS, kMinBlocks)
     float (*vx)[TX + 8] = kStag ? sCxv : sCx;
     float (*vy)[TY + 8] = kStag ? sCyv : sCy;
     const Geom &G = A.g;
-    const int x0 = (blockIdx.x % A.tiles_x) * TX, y0 = (blockIdx.x / A.tiles_x) * TY;
+    const int tile = tile_of_block(A, blockIdx.x);
+    const int x0 = (tile % A.tiles_x) * TX, y0 = (tile / A.tiles_x) * TY;
     int z0, z1;
     chunk_range(A, blockIdx.y, &z0, &z1);
     const bool interior = x0 - 4 >= G.lo[0] && x0 + TX + 4 <= G.nx - G.hi[0] && y0 - 4 >= G.lo[1] &&
