@@ -56,7 +56,7 @@ typedef enum {
     FDTD_EUNSTABLE = 5,    /* c_max dt / h above the scheme's stability limit */
     FDTD_EDIVERGED = 6,    /* non-finite values detected */
     FDTD_ETIMEOUT = 7,     /* a bounded device-side wait gave up */
-    FDTD_EUNSUPPORTED = 8  /* valid request this build does not provide */
+    FDTD_EUNSUPPORTED = 8  /* valid request the library does not provide */
 } fdtd_status;
 
 typedef enum {
@@ -285,7 +285,7 @@ int fdtd_set_field(fdtd_ctx *ctx, int which, int shot, const float *src_dev);
  * reads src's arrays directly: src's last step must be complete or on the
  * same stream.  The adjoint state and checkpoints are not exchanged.  Both
  * contexts must live on the same GPU (EUNSUPPORTED otherwise: parts on
- * several GPUs would need peer access, which this build does not set up). */
+ * several GPUs would need peer access, which the library does not set up). */
 int fdtd_exchange(fdtd_ctx *dst, const fdtd_ctx *src, const int box[6], const int shift[3]);
 
 /* Zero every field and memory variable, time index 0 (model, CPML, source and

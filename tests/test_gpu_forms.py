@@ -76,7 +76,7 @@ def test_f32_storage_within_its_tolerance(oracle128):
 
 
 def test_f16_storage_within_budget_while_the_wave_is_in_the_grid(oracle128):
-    """The benchmark spec's 2e-2 relative L2 budget, asserted as stated, for the
+    """The precision form's 2e-2 relative L2 budget, asserted as stated, for the
     pressure after 250 and 375 steps and for the traces of the whole run."""
     e = _gpu_errors(oracle128, "f16")
     assert e[250] <= 2e-2 and e[375] <= 2e-2 and e["traces"] <= 2e-2, e
