@@ -59,10 +59,13 @@ def test_homogeneous_64_full_run_matches_oracle():
     ((70, 37, 150), (3, 5, 2, 4, 6, 1), "7"),
     ((40, 33, 70), (0, 0, 0, 0, 0, 0), "9"),
     ((24, 20, 64), (8, 8, 8, 8, 8, 8), None),
+    # x layers reaching two tile columns on each side (launched before the others)
+    ((20, 36, 200), (30, 33, 2, 3, 2, 2), None),
 ])
 def test_ragged_grids_random_state_all_fields(shape, cells, zchunk, monkeypatch):
     """Random state on grids that span several tiles with ragged tails, unequal
-    layers per face, z-chunk boundaries and no layer at all: 5 steps."""
+    layers per face, z-chunk boundaries, no layer at all, and x layers wide enough
+    that two tile columns per face carry them: 5 steps."""
     if zchunk:
         monkeypatch.setenv("FDTD_ZCHUNK", zchunk)
     Fdtd = _fdtd()
