@@ -157,13 +157,16 @@ def measured_peaks():
 
 
 def step_kernel_source_hash() -> str:
-    """Hash of the step kernel's device code: fdtd_step.cu and the shared
-    declarations of fdtd_internal.cuh up to the host-only context struct."""
+    """Hash of what decides a step kernel launch: its device code (fdtd_step.cu
+    and the shared declarations of fdtd_internal.cuh up to the host-only
+    context struct) and the host code that sets its launch (fdtd_api.cu: the
+    z-chunking, the tile order's columns, the arguments)."""
     csrc = os.path.join(ROOT, "paper_2606_06910_gb300", "csrc")
     step = open(os.path.join(csrc, "fdtd_step.cu"), "rb").read()
     inc = open(os.path.join(csrc, "fdtd_internal.cuh"), "rb").read()
+    api = open(os.path.join(csrc, "fdtd_api.cu"), "rb").read()
     cut = inc.find(b"// The opaque context behind fdtd_ctx*.")
-    return hashlib.sha256(step + (inc[:cut] if cut >= 0 else inc)).hexdigest()[:16]
+    return hashlib.sha256(step + (inc[:cut] if cut >= 0 else inc) + api).hexdigest()[:16]
 
 
 def step_kernel_traffic(storage: str, shape, variant: str = "plain"):
