@@ -294,13 +294,15 @@ void choose_zchunk(fdtd_ctx *c)
             best = zc;
         }
     }
-    // Large grids: chunks of about 48 planes (FP32) or 256 (16-bit storage).
-    // CTAs that start together on chunks of moderate length stay close in z,
-    // so the halo planes that neighbouring tiles read are still in L2, while
-    // fewer chunk ends are re-read.  With the x-layer tiles launched first,
-    // 48 / 256 measured best on 512^3 and 1024^3 (FP32 1.049 ms at 512^3
-    // against 1.069 with 32; FP16 6.97 ms at 1024^3 against 7.16 with 96).
-    int target = c->d.storage == FDTD_F32 ? 48 : 256;
+    // Large grids: chunks of about 48 planes (FP32); with 16-bit storage 96,
+    // or 256 from 768 planes on.  CTAs that start together on chunks of
+    // moderate length stay close in z, so the halo planes that neighbouring
+    // tiles read are still in L2, while fewer chunk ends are re-read; at 512
+    // planes the wave count decides between the longer chunks.  Measured with
+    // the x-layer tiles launched first: FP32 1.049 ms at 512^3 against 1.069
+    // with 32, 7.45 ms at 1024^3 against 7.66; FP16 6.97 ms at 1024^3 against
+    // 7.16 with 96, and 1.021 ms at 512^3 against 1.092 with 256.
+    int target = c->d.storage == FDTD_F32 ? 48 : (c->g.nz >= 768 ? 256 : 96);
     if (const char *e = getenv("FDTD_ZTARGET"))   // tuning: planes per middle chunk
         target = std::max(8, atoi(e));
     const int kt = (nz + target - 1) / target;
